@@ -1,0 +1,189 @@
+"""Seeded synthetic inputs shaped like the paper's workloads (Sec. 4.1).
+
+This module is the only code that both the CUDA path's callers and the oracle's callers
+use: it draws random matrices and nothing else.  It holds none of the factorisation's
+arithmetic (no QR, Cholesky or eigensolver): random orthogonal factors come from the
+Cayley transform of a random skew-symmetric matrix (one dense linear solve).
+
+All host matrices are returned column-major (numpy Fortran order), m x n.
+Device matrices are returned as torch tensors of shape (n, m), row-major, which is the
+same memory as an m x n column-major matrix with leading dimension m.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+
+# --------------------------------------------------------------------------- host
+
+
+def gaussian(m: int, n: int, seed: int, dtype=np.float64) -> np.ndarray:
+    """X with i.i.d. N(0,1) entries (the plain workload of Sec. 4.1)."""
+    rng = np.random.default_rng(seed)
+    return np.asfortranarray(rng.standard_normal((n, m)).T.astype(dtype))
+
+
+def random_orthogonal(n: int, rng: np.random.Generator) -> np.ndarray:
+    """A random n x n orthogonal matrix: Cayley transform (I - K)(I + K)^{-1}, K skew."""
+    A = rng.standard_normal((n, n))
+    K = (A - A.T) / (2.0 * math.sqrt(max(n, 1)))
+    eye = np.eye(n)
+    # (I - K)(I + K)^{-1} = solve((I + K)^T, (I - K)^T)^T
+    return np.linalg.solve((eye + K).T, (eye - K).T).T
+
+
+def spectrum(n: int, kappa: float) -> np.ndarray:
+    """sigma_i = kappa^{-(i-1)/(n-1)}: geometric from 1 down to 1/kappa (sigma = 1 for n = 1)."""
+    if n == 1:
+        return np.ones(1)
+    return kappa ** (-np.arange(n) / (n - 1.0))
+
+
+def mixing_matrix(n: int, kappa: float, seed: int) -> np.ndarray:
+    """S = V diag(sigma) W^T with V, W random orthogonal, so that X = G S has kappa_2 ~ kappa."""
+    rng = np.random.default_rng(seed + 7919)
+    V = random_orthogonal(n, rng)
+    W = random_orthogonal(n, rng)
+    return (V * spectrum(n, kappa)) @ W.T
+
+
+def conditioned(m: int, n: int, kappa: float, seed: int, dtype=np.float64) -> np.ndarray:
+    """X = G S with G m x n i.i.d. N(0,1) and S = V diag(sigma) W^T (condition sweep)."""
+    G = gaussian(m, n, seed)
+    X = G @ mixing_matrix(n, kappa, seed)
+    return np.asfortranarray(X.astype(dtype))
+
+
+def hadamard_columns(m: int, n: int) -> np.ndarray:
+    """First n columns of the m x m Sylvester Hadamard matrix (m a power of two):
+    H_ij = (-1)^popcount(i & j), so H^T H = m I."""
+    if m & (m - 1) or m < n:
+        raise ValueError("m must be a power of two and >= n")
+    i = np.arange(m, dtype=np.int64)
+    H = np.empty((m, n), order="F")
+    for j in range(n):
+        H[:, j] = 1.0 - 2.0 * (np.bitwise_count(i & j) & 1)
+    return H
+
+
+def small_upper(n: int, seed: int, lo: int = -3, hi: int = 3) -> np.ndarray:
+    """A small-integer upper triangular R0: off-diagonal entries in lo..hi, diagonal in
+    2n+1..2n+4 (rows are diagonally dominant, so R0 stays well conditioned at n = 64)."""
+    rng = np.random.default_rng(seed + 104729)
+    R0 = np.triu(rng.integers(lo, hi + 1, size=(n, n))).astype(np.float64)
+    R0[np.diag_indices(n)] = rng.integers(2 * n + 1, 2 * n + 5, size=n)
+    return R0
+
+
+def hadamard_case(m: int, n: int, seed: int, dtype=np.float64):
+    """(X, R_exact): X = H[:, :n] R0 is an exact integer matrix and R = sqrt(m) R0 exactly."""
+    R0 = small_upper(n, seed)
+    X = hadamard_columns(m, n) @ R0
+    return np.asfortranarray(X.astype(dtype)), math.sqrt(m) * R0
+
+
+def lstsq_case(m: int, n: int, kappa: float, seed: int, noise: float = 1e-6, dtype=np.float64):
+    """(A, b, x_star): A = G S (kappa), x* ~ N(0,1), b = A x* + noise * N(0,1)."""
+    A = conditioned(m, n, kappa, seed)
+    rng = np.random.default_rng(seed + 31337)
+    x_star = rng.standard_normal(n)
+    b = A @ x_star + noise * rng.standard_normal(m)
+    return np.asfortranarray(A.astype(dtype)), b.astype(dtype), x_star
+
+
+# --------------------------------------------------------------------------- device
+
+
+def conditioned_device(m: int, n: int, kappa: float, seed: int, device="cuda", dtype=None,
+                       chunk_rows: int = 1 << 22):
+    """Device-resident X = G S as a (n, m) torch tensor (column-major m x n, ld = m).
+
+    G is drawn by torch's seeded device generator in row chunks; S comes from the same
+    host recipe as `conditioned`.  For kappa == 1 and S = I the plain Gaussian is returned.
+    """
+    import torch
+
+    dtype = dtype or torch.float64
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    S = torch.from_numpy(mixing_matrix(n, kappa, seed)).to(device=device, dtype=torch.float64)
+    Xt = torch.empty((n, m), dtype=dtype, device=device)
+    for r0 in range(0, m, chunk_rows):
+        r1 = min(m, r0 + chunk_rows)
+        Gt = torch.randn((n, r1 - r0), generator=g, device=device, dtype=torch.float64)
+        Xt[:, r0:r1] = (S.T @ Gt).to(dtype)
+    return Xt
+
+
+def hadamard_device(m: int, n: int, seed: int, device="cuda", dtype=None):
+    """Device-resident Hadamard case: ((n, m) tensor, R_exact numpy)."""
+    import torch
+
+    dtype = dtype or torch.float64
+    R0 = small_upper(n, seed)
+    i = torch.arange(m, device=device, dtype=torch.int64)
+    Xt = torch.zeros((n, m), dtype=torch.float64, device=device)
+    for j in range(n):
+        b = i & j
+        par = torch.zeros_like(b)
+        for _ in range(max(j.bit_length(), 1)):  # parity of popcount(i & j)
+            par ^= b & 1
+            b = b >> 1
+        h = 1.0 - 2.0 * par.to(torch.float64)
+        # X[:, c] += H[:, j] * R0[j, c]  (R0 is upper triangular)
+        Xt += torch.from_numpy(R0[j, :]).to(device).unsqueeze(1) * h.unsqueeze(0)
+    return Xt.to(dtype), math.sqrt(m) * R0
+
+
+# --------------------------------------------------------------------------- batched / serving
+
+
+@dataclass
+class Instance:
+    m: int
+    n: int
+    kappa: float
+    seed: int
+    dtype: str = "f64"
+    kind: str = "qr"  # "qr" or "lstsq"
+
+
+def batched_instances(count: int = 512, seed: int = 4, m_lo: int = 1 << 10, m_hi: int = 1 << 20,
+                      n_lo: int = 4, n_hi: int = 48, kappa_hi: float = 1e6):
+    """Uneven batch: m log-uniform in [m_lo, m_hi], n uniform in {n_lo..n_hi},
+    kappa log-uniform in [1, kappa_hi]."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(count):
+        m = int(round(math.exp(rng.uniform(math.log(m_lo), math.log(m_hi)))))
+        n = int(rng.integers(n_lo, n_hi + 1))
+        kappa = float(math.exp(rng.uniform(0.0, math.log(kappa_hi))))
+        out.append(Instance(max(m, n), n, kappa, seed * 100003 + k))
+    return out
+
+
+@dataclass
+class Request(Instance):
+    arrival_s: float = 0.0
+
+
+def serving_stream(count: int = 20000, rate_per_s: float = 2000.0, seed: int = 5,
+                   m_lo: int = 1 << 12, m_hi: int = 1 << 22, n_lo: int = 2, n_hi: int = 64,
+                   frac_f32: float = 0.3, frac_lstsq: float = 0.2, kappa_hi: float = 1e6):
+    """Poisson arrivals at `rate_per_s`; m log-uniform, n uniform, 30% FP32-stored,
+    20% least-squares requests, kappa log-uniform in [1, kappa_hi]."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for k in range(count):
+        t += float(rng.exponential(1.0 / rate_per_s))
+        m = int(round(math.exp(rng.uniform(math.log(m_lo), math.log(m_hi)))))
+        n = int(rng.integers(n_lo, n_hi + 1))
+        dtype = "f32" if rng.uniform() < frac_f32 else "f64"
+        kind = "lstsq" if rng.uniform() < frac_lstsq else "qr"
+        kappa = float(math.exp(rng.uniform(0.0, math.log(kappa_hi))))
+        out.append(Request(max(m, n + 1), n, kappa, seed * 1000003 + k, dtype, kind, t))
+    return out
