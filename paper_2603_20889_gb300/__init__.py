@@ -1,0 +1,204 @@
+"""qless: Q-less QR of tall, very skinny matrices on GB300 -- Python binding.
+
+A thin ctypes layer over the C ABI in include/qless.h (libqless.so, built in-tree by
+``build.py``).  It marshals arguments only: every step of every factorisation runs in the
+library's CUDA kernels.  PyTorch provides device memory and the current stream.
+
+Matrices are column-major: an m x n matrix is a torch tensor of shape (m, n) with
+stride(0) == 1 (for example ``Xt.T`` for a contiguous (n, m) tensor ``Xt``); its leading
+dimension is stride(1).
+
+Raw entry points (same names and argument order as the C ABI) are available as
+``lib.ql_tsqr_qless`` etc.; the functions below are conveniences that allocate outputs
+and workspace with torch.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libqless.so")
+
+QL_OK, QL_ERR_ARG, QL_ERR_ALIGN, QL_ERR_WORKSPACE, QL_ERR_CUDA = 0, 1, 2, 3, 4
+QL_ERR_NOT_SPD, QL_ERR_TIMEOUT, QL_ERR_NONFINITE, QL_ERR_BUDGET, QL_ERR_BUSY, QL_ERR_UNKNOWN = 5, 6, 7, 8, 9, 10
+QL_F64, QL_F32 = 0, 1
+QL_TSQR, QL_CHOLQR2, QL_SVQB2, QL_AUTO = 0, 1, 2, 3
+QL_ARITH_DF, QL_ARITH_F64 = 0, 1
+
+STATUS_NAMES = {0: "QL_OK", 1: "QL_ERR_ARG", 2: "QL_ERR_ALIGN", 3: "QL_ERR_WORKSPACE", 4: "QL_ERR_CUDA",
+                5: "QL_ERR_NOT_SPD", 6: "QL_ERR_TIMEOUT", 7: "QL_ERR_NONFINITE", 8: "QL_ERR_BUDGET",
+                9: "QL_ERR_BUSY", 10: "QL_ERR_UNKNOWN"}
+
+# Every symbol include/qless.h declares, with its ctypes signature.
+_i64, _i32, _vp, _dp, _sz, _f64 = ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_double
+SIGNATURES = {
+    "ql_set_arith": (_i32, [_i32]),
+    "ql_version": (ctypes.c_char_p, []),
+    "ql_workspace_bytes": (_sz, [_i32, _i64, _i64, _i32]),
+    "ql_tsqr_qless": (_i32, [_i64, _i64, _vp, _i32, _i64, _dp, _i64, _vp, _vp, _sz, _vp]),
+    "ql_cholqr2_qless": (_i32, [_i64, _i64, _vp, _i32, _i64, _dp, _i64, _vp, _vp, _sz, _vp]),
+    "ql_svqb_qless": (_i32, [_i64, _i64, _vp, _i32, _i64, _dp, _i64, _dp, _f64, _vp, _vp, _sz, _vp]),
+    "ql_lstsq_qless": (_i32, [_i64, _i64, _vp, _i64, _vp, _i32, _i32, _dp, _dp, _dp, _vp, _vp, _sz, _vp]),
+    "ql_batch_workspace_bytes": (_sz, [_i32, _vp]),
+    "ql_batch_qless": (_i32, [_i32, _vp, _vp, _sz, _vp]),
+    "ql_autotune_workspace_bytes": (_sz, [_i64, _i64, _i32]),
+    "ql_autotune": (_i32, [_i64, _i64, _i32, _f64, _vp, _sz, _vp, _vp, _vp]),
+    "ql_autotune_save": (_i32, [ctypes.c_char_p]),
+    "ql_autotune_load": (_i32, [ctypes.c_char_p]),
+    "ql_autotune_choose": (_i32, [_i64, _i64, _i32, _f64]),
+    "ql_server_create": (_vp, [_sz, _i32, _i32]),
+    "ql_server_submit": (_i32, [_vp, _vp, _vp]),
+    "ql_server_poll": (_i32, [_vp, ctypes.c_uint64, _vp]),
+    "ql_server_release": (_i32, [_vp, ctypes.c_uint64]),
+    "ql_server_drain": (_i32, [_vp, _f64]),
+    "ql_server_stats": (_i32, [_vp, _vp]),
+    "ql_server_destroy": (None, [_vp]),
+}
+
+
+class QlError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = int(status)
+        super().__init__(f"{what}: {STATUS_NAMES.get(self.status, self.status)}")
+
+
+_lib = None
+
+
+def load_library(path: str | None = None):
+    """Load libqless.so (raises if it was not built: there is no fallback path)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise ImportError(f"qless CUDA library not built: {p} is missing (run build.py / __graft_entry__.build())")
+    lib = ctypes.CDLL(p)
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(lib, name, None)
+        if f is None:
+            continue
+        f.restype = res
+        f.argtypes = args
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def __getattr__(name):
+    if name == "lib":
+        return load_library()
+    raise AttributeError(name)
+
+
+# ------------------------------------------------------------------ torch conveniences
+
+
+def _torch():
+    import torch
+
+    return torch
+
+
+def _stream_ptr(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _colmajor(X):
+    """(m, n, ld, dtype code) of a column-major (m, n) tensor view."""
+    torch = _torch()
+    if X.dim() == 1:
+        X = X.unsqueeze(1)
+    m, n = X.shape
+    if X.dtype == torch.float64:
+        dt = QL_F64
+    elif X.dtype == torch.float32:
+        dt = QL_F32
+    else:
+        raise TypeError("X must be float64 or float32")
+    if not X.is_cuda:
+        raise TypeError("X must be a CUDA tensor")
+    if n > 1 and X.stride(0) != 1:
+        raise ValueError("X must be column-major: an (m, n) view with stride(0) == 1 (e.g. Xt.T)")
+    ld = X.stride(1) if n > 1 else max(m, 1)
+    return m, n, max(ld, max(m, 1)), dt
+
+
+def set_arith(mode: int) -> int:
+    return load_library().ql_set_arith(mode)
+
+
+def workspace(method: int, m: int, n: int, dtype: int, device=None):
+    torch = _torch()
+    nb = load_library().ql_workspace_bytes(method, m, n, dtype)
+    if nb == 0:
+        raise QlError(QL_ERR_ARG, "ql_workspace_bytes")
+    return torch.empty(nb, dtype=torch.uint8, device=device or "cuda")
+
+
+def _check(st, what):
+    if st != QL_OK:
+        raise QlError(st, what)
+
+
+def tsqr_qless(X, R=None, info=None, ws=None, stream=None):
+    """R (n x n, float64, column-major) of X by Q-less Householder TSQR.  Returns (R, info)."""
+    torch = _torch()
+    m, n, ld, dt = _colmajor(X)
+    R = R if R is not None else torch.empty((n, n), dtype=torch.float64, device=X.device).T
+    info = info if info is not None else torch.zeros(2, dtype=torch.int32, device=X.device)
+    ws = ws if ws is not None else workspace(QL_TSQR, m, n, dt, X.device)
+    st = load_library().ql_tsqr_qless(m, n, X.data_ptr(), dt, ld, R.data_ptr(), R.stride(1) if n > 1 else n,
+                                      info.data_ptr(), ws.data_ptr(), ws.numel(), _stream_ptr(stream))
+    _check(st, "ql_tsqr_qless")
+    return R, info
+
+
+def cholqr2_qless(X, R=None, info=None, ws=None, stream=None):
+    """R of X by Q-less Cholesky-QR2 (Algorithm 1).  Returns (R, info)."""
+    torch = _torch()
+    m, n, ld, dt = _colmajor(X)
+    R = R if R is not None else torch.empty((n, n), dtype=torch.float64, device=X.device).T
+    info = info if info is not None else torch.zeros(2, dtype=torch.int32, device=X.device)
+    ws = ws if ws is not None else workspace(QL_CHOLQR2, m, n, dt, X.device)
+    st = load_library().ql_cholqr2_qless(m, n, X.data_ptr(), dt, ld, R.data_ptr(), R.stride(1) if n > 1 else n,
+                                         info.data_ptr(), ws.data_ptr(), ws.numel(), _stream_ptr(stream))
+    _check(st, "ql_cholqr2_qless")
+    return R, info
+
+
+def svqb_qless(X, R=None, Z=None, rank_tol=0.0, info=None, ws=None, stream=None, want_z=False):
+    """R (and optionally Z of X = Q Z) by Q-less SVQB2.  Returns (R, Z or None, info)."""
+    torch = _torch()
+    m, n, ld, dt = _colmajor(X)
+    R = R if R is not None else torch.empty((n, n), dtype=torch.float64, device=X.device).T
+    if want_z and Z is None:
+        Z = torch.empty((n, n), dtype=torch.float64, device=X.device).T
+    info = info if info is not None else torch.zeros(2, dtype=torch.int32, device=X.device)
+    ws = ws if ws is not None else workspace(QL_SVQB2, m, n, dt, X.device)
+    st = load_library().ql_svqb_qless(m, n, X.data_ptr(), dt, ld, R.data_ptr(), R.stride(1) if n > 1 else n,
+                                      Z.data_ptr() if Z is not None else None, float(rank_tol), info.data_ptr(),
+                                      ws.data_ptr(), ws.numel(), _stream_ptr(stream))
+    _check(st, "ql_svqb_qless")
+    return R, Z, info
+
+
+def lstsq_qless(A, b, method=QL_TSQR, want_rext=False, info=None, ws=None, stream=None):
+    """min ||A x - b|| via the Q-less QR of [A b].  Returns (x, resnorm, R_ext or None, info)."""
+    torch = _torch()
+    m, n, ld, dt = _colmajor(A)
+    if b.dtype != A.dtype or b.numel() != m or (b.dim() == 2 and b.stride(0) != 1):
+        raise ValueError("b must have m contiguous entries of A's dtype")
+    x = torch.empty(n, dtype=torch.float64, device=A.device)
+    rn = torch.empty(1, dtype=torch.float64, device=A.device)
+    Rext = torch.empty((n + 1, n + 1), dtype=torch.float64, device=A.device).T if want_rext else None
+    info = info if info is not None else torch.zeros(2, dtype=torch.int32, device=A.device)
+    ws = ws if ws is not None else workspace(QL_AUTO, m, n, dt, A.device)
+    st = load_library().ql_lstsq_qless(m, n, A.data_ptr(), ld, b.data_ptr(), dt, method, x.data_ptr(),
+                                       rn.data_ptr(), Rext.data_ptr() if Rext is not None else None,
+                                       info.data_ptr(), ws.data_ptr(), ws.numel(), _stream_ptr(stream))
+    _check(st, "ql_lstsq_qless")
+    return x, rn, Rext, info

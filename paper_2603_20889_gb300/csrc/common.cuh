@@ -1,0 +1,244 @@
+// Shared device building blocks of the qless kernels: double-float arithmetic, the two
+// arithmetic policies (double-float on the FP32 pipes, native FP64), cp.async staging and
+// the small FP64 n x n routines that run inside the "last CTA done" epilogues.
+#pragma once
+
+#include <cstdint>
+#include <type_traits>
+#include <cuda_runtime.h>
+
+#include "../../include/qless.h"
+
+#define QL_DEV __device__ __forceinline__
+
+namespace ql {
+
+constexpr int kMaxN = 64;
+
+// ---------------------------------------------------------------------------------------
+// Double-float ("df"): value = hi + lo with |lo| <= ulp(hi).  Error-free transformations
+// use the _rn intrinsics so that nvcc never contracts or reassociates them.
+//   two_sum (Knuth), fast_two_sum (Dekker, |a| >= |b|), two_prod via FMA.
+// ---------------------------------------------------------------------------------------
+struct df {
+  float hi, lo;
+};
+
+QL_DEV void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+QL_DEV void fast_two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  e = __fsub_rn(b, __fsub_rn(s, a));
+}
+QL_DEV df df_make(float hi, float lo) {
+  df r;
+  fast_two_sum(hi, lo, r.hi, r.lo);
+  return r;
+}
+QL_DEV df df_add(df a, df b) {  // "sloppy" sum: absolute error ~ u^2 (|a| + |b|)
+  float s, e;
+  two_sum(a.hi, b.hi, s, e);
+  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  return df_make(s, e);
+}
+QL_DEV df df_neg(df a) { return df{-a.hi, -a.lo}; }
+QL_DEV df df_sub(df a, df b) { return df_add(a, df_neg(b)); }
+QL_DEV df df_mul(df a, df b) {
+  float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return df_make(p, e);
+}
+// a - b * c, one renormalisation.
+QL_DEV df df_sub_mul(df a, df b, df c) {
+  float p = __fmul_rn(b.hi, c.hi);
+  float e = __fmaf_rn(b.hi, c.hi, -p);
+  e = __fmaf_rn(b.hi, c.lo, e);
+  e = __fmaf_rn(b.lo, c.hi, e);
+  float s, t;
+  two_sum(a.hi, -p, s, t);
+  t = __fadd_rn(t, __fsub_rn(a.lo, e));
+  return df_make(s, t);
+}
+QL_DEV df df_recip(df b) {  // 1 / b: one Newton correction of the float reciprocal
+  float q = __fdiv_rn(1.0f, b.hi);
+  float p = __fmul_rn(q, b.hi);
+  float e = __fmaf_rn(q, b.hi, -p);
+  e = __fmaf_rn(q, b.lo, e);
+  float r = __fsub_rn(__fsub_rn(1.0f, p), e);  // 1 - q b
+  return df_make(q, __fmul_rn(r, q));
+}
+QL_DEV df df_sqrt(df a) {  // sqrt(a), a >= 0: one Newton correction of sqrtf
+  if (a.hi <= 0.0f) return df{0.0f, 0.0f};
+  float s = __fsqrt_rn(a.hi);
+  float p = __fmul_rn(s, s);
+  float e = __fmaf_rn(s, s, -p);
+  float r = __fadd_rn(__fsub_rn(__fsub_rn(a.hi, p), e), a.lo);
+  return df_make(s, __fdiv_rn(r, __fmul_rn(2.0f, s)));
+}
+QL_DEV double df_to_double(df a) { return (double)a.hi + (double)a.lo; }
+QL_DEV df df_from_double_rn(double x) {  // used only on n x n data
+  float hi = __double2float_rn(x);
+  float lo = __double2float_rn(x - (double)hi);
+  return df{hi, lo};
+}
+
+// Split an IEEE double into a double-float with integer operations only (the FP64 pipe is
+// the scarce resource on this GPU): hi = the top 24 significand bits, lo = the next 23,
+// both truncated, so |x - (hi + lo)| < 2^-47 |x|.  Zero and subnormals give 0.
+// The biased exponent E of x is returned for the range check.
+QL_DEV df df_split_double(double x, int& E) {
+  unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  unsigned int hw = (unsigned int)(bits >> 32), lw = (unsigned int)bits;
+  unsigned int sign = hw & 0x80000000u;
+  E = (int)((hw >> 20) & 0x7ffu);
+  if (E < 920 || E > 1150) {  // out of the double-float range (zero included): flag via E
+    df z{0.0f, 0.0f};
+    if (E > 1150 && E < 2047) z.hi = __int_as_float((int)(sign | 0x7f000000u));  // huge: keep order
+    return z;
+  }
+  unsigned int hb = sign | ((unsigned int)(E - 896) << 23) | ((hw & 0xfffffu) << 3) | (lw >> 29);
+  unsigned int eb = sign | ((unsigned int)(E - 919) << 23);
+  unsigned int lb = eb | ((lw >> 6) & 0x7fffffu);
+  df r;
+  r.hi = __int_as_float((int)hb);
+  r.lo = __fsub_rn(__int_as_float((int)lb), __int_as_float((int)eb));
+  return r;
+}
+
+QL_DEV df shfl_xor(df a, int mask) {
+  return df{__shfl_xor_sync(0xffffffffu, a.hi, mask), __shfl_xor_sync(0xffffffffu, a.lo, mask)};
+}
+
+// ---------------------------------------------------------------------------------------
+// Arithmetic policies.  T is the working element; Acc an unnormalised dot-product
+// accumulator; load() converts one stored element and reports its biased IEEE-double
+// exponent in E for the range check (only the double-float policy needs it).
+// ---------------------------------------------------------------------------------------
+struct ArithDF {
+  using T = df;
+  struct Acc {
+    float hi, lo;
+  };
+  static constexpr bool kRangeChecked = true;
+  QL_DEV static T zero() { return df{0.0f, 0.0f}; }
+  // Convert one stored element; E receives its biased IEEE-double exponent (0 for zero).
+  QL_DEV static T load(double x, int& E) { return df_split_double(x, E); }
+  QL_DEV static T load(float x, int& E) {
+    int e = (__float_as_int(x) >> 23) & 0xff;
+    E = e == 0 ? 0 : e + 896;  // rebias to the double exponent scale
+    return e == 0 ? df{0.0f, 0.0f} : df{x, 0.0f};
+  }
+  QL_DEV static Acc acc_zero() { return Acc{0.0f, 0.0f}; }
+  QL_DEV static void acc_fma(Acc& acc, T a, T b) {  // acc += a * b
+    float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    float s, t;
+    two_sum(acc.hi, p, s, t);
+    acc.hi = s;
+    acc.lo = __fadd_rn(acc.lo, __fadd_rn(t, e));
+  }
+  QL_DEV static T acc_get(Acc a) { return df_make(a.hi, a.lo); }
+  QL_DEV static T add(T a, T b) { return df_add(a, b); }
+  QL_DEV static T sub(T a, T b) { return df_sub(a, b); }
+  QL_DEV static T mul(T a, T b) { return df_mul(a, b); }
+  QL_DEV static T sub_mul(T a, T b, T c) { return df_sub_mul(a, b, c); }
+  QL_DEV static T recip(T a) { return df_recip(a); }
+  QL_DEV static T sqrt_(T a) { return df_sqrt(a); }
+  QL_DEV static T neg(T a) { return df_neg(a); }
+  QL_DEV static bool is_zero(T a) { return a.hi == 0.0f; }
+  QL_DEV static bool negative(T a) { return a.hi < 0.0f; }
+  QL_DEV static double to_double(T a) { return df_to_double(a); }
+  QL_DEV static T from_double(double x) { return df_from_double_rn(x); }
+  QL_DEV static T shfl(T a, int mask) { return shfl_xor(a, mask); }
+};
+
+struct ArithF64 {
+  using T = double;
+  using Acc = double;
+  static constexpr bool kRangeChecked = false;
+  QL_DEV static T zero() { return 0.0; }
+  QL_DEV static T load(double x, int& E) {
+    E = 0;
+    return x;
+  }
+  QL_DEV static T load(float x, int& E) {
+    E = 0;
+    return (double)x;
+  }
+  QL_DEV static Acc acc_zero() { return 0.0; }
+  QL_DEV static void acc_fma(Acc& acc, T a, T b) { acc = fma(a, b, acc); }
+  QL_DEV static T acc_get(Acc a) { return a; }
+  QL_DEV static T add(T a, T b) { return a + b; }
+  QL_DEV static T sub(T a, T b) { return a - b; }
+  QL_DEV static T mul(T a, T b) { return a * b; }
+  QL_DEV static T sub_mul(T a, T b, T c) { return fma(-b, c, a); }
+  QL_DEV static T recip(T a) { return 1.0 / a; }
+  QL_DEV static T sqrt_(T a) { return a > 0.0 ? sqrt(a) : 0.0; }
+  QL_DEV static T neg(T a) { return -a; }
+  QL_DEV static bool is_zero(T a) { return a == 0.0; }
+  QL_DEV static bool negative(T a) { return a < 0.0; }
+  QL_DEV static double to_double(T a) { return a; }
+  QL_DEV static T from_double(double x) { return x; }
+  QL_DEV static T shfl(T a, int mask) { return __shfl_xor_sync(0xffffffffu, a, mask); }
+};
+
+// Range accepted by the double-float kernels: every nonzero block-column maximum |x| in
+// [2^-40, 2^50] (biased double exponents 983..1073); the per-thread minimum exponent is
+// only used to detect columns whose block maximum is tiny.
+constexpr int kDfEmaxLimit = 1023 + 50;
+constexpr int kDfEminLimit = 1023 - 40;
+
+// ---------------------------------------------------------------------------------------
+// cp.async staging (Ampere-style per-thread async copies; any element-aligned address).
+// ---------------------------------------------------------------------------------------
+template <int I, int N, typename F>
+QL_DEV void static_for(F&& f) {
+  if constexpr (I < N) {
+    f(std::integral_constant<int, I>{});
+    static_for<I + 1, N>(f);
+  }
+}
+
+QL_DEV unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+QL_DEV void cp_async_8(void* smem, const void* gmem, bool valid) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(smem_addr(smem)), "l"(gmem),
+               "r"(valid ? 8 : 0));
+}
+QL_DEV void cp_async_4(void* smem, const void* gmem, bool valid) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(smem_addr(smem)), "l"(gmem),
+               "r"(valid ? 4 : 0));
+}
+QL_DEV void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+QL_DEV void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+template <typename S>
+QL_DEV void cp_async_elem(S* smem, const S* gmem, bool valid);
+template <>
+QL_DEV void cp_async_elem<double>(double* smem, const double* gmem, bool valid) {
+  cp_async_8(smem, gmem, valid);
+}
+template <>
+QL_DEV void cp_async_elem<float>(float* smem, const float* gmem, bool valid) {
+  cp_async_4(smem, gmem, valid);
+}
+
+// Column pointer of the logical matrix [A b]: columns < nA come from A (ld lda), column nA
+// (if any) from the vector b.  Used so least squares reads [A b] in place.
+template <typename S>
+struct ColSource {
+  const S* A;
+  int64_t lda;
+  const S* b;
+  int nA;
+  QL_DEV const S* col(int c) const { return c < nA ? A + (int64_t)c * lda : b; }
+};
+
+}  // namespace ql

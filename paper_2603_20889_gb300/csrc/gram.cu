@@ -1,0 +1,47 @@
+// Host launcher of the Q-less Gram methods (paper Sec. 3.1): Cholesky-QR2 (Algorithm 1)
+// and SVQB2.  Two launches per call (first pass, second pass); after the double-float
+// pair, two gated FP64 launches follow that run only if the range check fired.
+#include "gram_launch.cuh"
+
+namespace ql {
+
+static int nc_of(int n) { return n <= 1 ? 1 : n <= 2 ? 2 : n <= 4 ? 4 : n <= 8 ? 8 : n <= 16 ? 16 : n <= 32 ? 32 : 64; }
+
+static size_t gram_layout(int n, GramWs* w, void* base) {
+  const int nc = nc_of(n);
+  const size_t head = 256;
+  const size_t keep = (size_t)3 * kMaxN * kMaxN * sizeof(double);
+  const size_t parts = (size_t)device_sm_count() * kGramMaxCtasPerSm * nc * nc * sizeof(double);
+  if (w && base) {
+    unsigned char* b = static_cast<unsigned char*>(base);
+    w->flags = reinterpret_cast<int*>(b);
+    w->keep = reinterpret_cast<double*>(b + head);
+    w->partials = reinterpret_cast<double*>(b + head + keep);
+  }
+  return head + keep + parts;
+}
+
+size_t gram_workspace_bytes(int n) {
+  if (n < 1 || n > kMaxN) return 0;
+  return gram_layout(n, nullptr, nullptr);
+}
+
+ql_status gram_launch(const GramCall& c, ql_arith arith) {
+  if (c.n < 1 || c.n > kMaxN) return QL_ERR_ARG;
+  if (c.method != QL_CHOLQR2 && c.method != QL_SVQB2) return QL_ERR_ARG;
+  if (!c.ws || c.ws_bytes < gram_layout(c.n, nullptr, nullptr)) return QL_ERR_WORKSPACE;
+  GramWs w;
+  gram_layout(c.n, &w, c.ws);
+  if (cudaMemsetAsync(w.flags, 0, 256, c.stream) != cudaSuccess) return QL_ERR_CUDA;
+  ql_status st;
+  if (c.dtype == QL_F64) {
+    if (arith == QL_ARITH_F64) return gram_dispatch<double, ArithF64>(c, w, 0);
+    if ((st = gram_dispatch<double, ArithDF>(c, w, 0))) return st;
+    return gram_dispatch<double, ArithF64>(c, w, 1);
+  }
+  if (arith == QL_ARITH_F64) return gram_dispatch<float, ArithF64>(c, w, 0);
+  if ((st = gram_dispatch<float, ArithDF>(c, w, 0))) return st;
+  return gram_dispatch<float, ArithF64>(c, w, 1);
+}
+
+}  // namespace ql

@@ -1,0 +1,72 @@
+// Host-side internal interfaces between the C ABI (api.cu) and the kernel translation
+// units.  Not part of the public boundary.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/qless.h"
+
+namespace ql {
+
+// Epilogue selected for the root of a TSQR / the last CTA of a Gram pass.
+enum Epilogue : int { kEpiR = 0, kEpiLstsq = 1 };
+
+struct TsqrCall {
+  int64_t m = 0;
+  int n = 0;            // columns factored (n + 1 for least squares)
+  int nA = 0;           // columns taken from A; column nA (if < n) comes from b
+  const void* A = nullptr;
+  int64_t lda = 0;
+  const void* b = nullptr;
+  ql_dtype dtype = QL_F64;
+  int epilogue = kEpiR;
+  double* R = nullptr;  // kEpiR: n x n output (ldr)
+  int64_t ldr = 0;
+  double* x = nullptr;  // kEpiLstsq: solution (n - 1 entries)
+  double* resnorm = nullptr;
+  double* Rext = nullptr;  // kEpiLstsq: optional n x n R_ext (ld n)
+  int32_t* info = nullptr;
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  cudaStream_t stream = nullptr;
+  int ctas_per_sm = 0;  // 0: occupancy maximum
+  int max_ctas = 0;     // 0: no limit (testing the R-tree with few leaves)
+};
+
+// Upper bound of the TSQR workspace for n columns (any m).
+size_t tsqr_workspace_bytes(int n);
+// Launch the double-float TSQR (or FP64 when arith == QL_ARITH_F64) and, after a
+// double-float launch, the gated FP64 fallback.
+ql_status tsqr_launch(const TsqrCall& c, ql_arith arith);
+
+struct GramCall {
+  int64_t m = 0;
+  int n = 0;
+  int nA = 0;
+  const void* A = nullptr;
+  int64_t lda = 0;
+  const void* b = nullptr;
+  ql_dtype dtype = QL_F64;
+  int method = QL_CHOLQR2;  // QL_CHOLQR2 or QL_SVQB2
+  int epilogue = kEpiR;
+  double* R = nullptr;
+  int64_t ldr = 0;
+  double* Z = nullptr;
+  double rank_tol = 0.0;
+  double* x = nullptr;
+  double* resnorm = nullptr;
+  double* Rext = nullptr;
+  int32_t* info = nullptr;
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  cudaStream_t stream = nullptr;
+};
+size_t gram_workspace_bytes(int n);
+ql_status gram_launch(const GramCall& c, ql_arith arith);
+
+int device_sm_count();
+ql_arith current_arith();
+
+}  // namespace ql

@@ -1,0 +1,401 @@
+// Q-less Householder TSQR device code (paper Sec. 3.2, Algorithms 2-4).
+//
+// A CTA owns a contiguous range of row blocks ("tiles") of X.  Each tile of b rows is
+// staged HBM -> shared memory with cp.async (issued one tile ahead, Algorithm 3's
+// asynchronous copy), moved into registers, and folded into the CTA's running triangle R
+// by the in-place trapezoidal Householder QR of [R; W] (Algorithm 4).  The per-CTA
+// triangles are merged by a binary R-tree inside the same launch (Algorithm 2's second
+// stage, replaced by "last CTA done" merges of triangle pairs), in FP64.
+//
+// Register tile layout: T threads = TC column groups x TR row threads.  Thread (cg, tr)
+// holds rows tr + q*TR (q < RPT) of the columns c = cg + k*TC (k < NCT = NC/TC), so the
+// work per Householder step shrinks evenly for every thread.  One shared-memory reduction
+// per column step yields the pivot column's norm and all its dot products at once:
+// for x = [R_jj; W(:,j)] and beta = -sign(R_jj) ||x||, v = x - beta e_1, the reflector
+// H = I - v v^T / (-beta v_1) (v_1 = R_jj - beta) updates column c > j by
+//   f_c = (W(:,j)^T W(:,c) + v_1 R_jc) / (-beta v_1),   R_jc -= v_1 f_c,   W(:,c) -= W(:,j) f_c.
+#pragma once
+
+#include "common.cuh"
+
+namespace ql {
+
+// Parameters of one TSQR problem as seen by the device code.
+template <typename S>
+struct TsqrProblem {
+  ColSource<S> src;  // columns of X (or of [A b])
+  int64_t m;         // rows
+  int n;             // columns (<= NC)
+};
+
+// Workspace views for one R-tree.
+struct TreeView {
+  double* slots;   // R triangles, n x n each (ld n), one per tree node
+  int* counters;   // one arrival counter per internal node
+  int* flags;      // [0]: range flag (double-float out of range), [1]: nonfinite
+  int leaves;      // number of leaves (CTAs contributing a triangle)
+};
+
+template <int NC, int TC, int RPT, int T>
+struct TsqrShape {
+  static constexpr int TR = T / TC;        // row threads per column group
+  static constexpr int NCT = NC / TC;      // columns held by one thread
+  static constexpr int B = TR * RPT;       // rows per tile
+  static_assert(NC % TC == 0, "column groups must divide NC");
+  static_assert(TR % 16 == 0 || TR == T, "row threads per group must be a multiple of 16");
+};
+
+// Shared-memory layout of the TSQR kernels.
+template <int NC, int TC, int RPT, int T, typename S, typename Ar>
+struct TsqrSmem {
+  using Sh = TsqrShape<NC, TC, RPT, T>;
+  using V = typename Ar::T;
+  static constexpr size_t kStage = sizeof(S) * NC * Sh::B;           // staged tile
+  static constexpr size_t kMerge = sizeof(double) * 2 * NC * NC;     // [Ra; Rb]
+  static constexpr size_t kArena = kStage > kMerge ? kStage : kMerge;
+  static constexpr size_t kR = sizeof(V) * NC * NC;                  // running triangle
+  static constexpr size_t kPart = sizeof(V) * NC * Sh::TR;           // column partial sums
+  static constexpr size_t kPiv = (TC > 1) ? sizeof(V) * Sh::B : 0;   // pivot broadcast
+  static constexpr size_t kF = sizeof(V) * NC;                       // reflector coefficients
+  static constexpr size_t kOffR = (kArena + 15) / 16 * 16;
+  static constexpr size_t kOffPart = kOffR + kR;
+  static constexpr size_t kOffPiv = kOffPart + kPart;
+  static constexpr size_t kOffF = kOffPiv + kPiv;
+  static constexpr size_t kOffMisc = kOffF + kF;                     // int[16] + int[NC]
+  static constexpr size_t kOffSd = (kOffMisc + (16 + NC) * sizeof(int) + 15) / 16 * 16;
+  static constexpr size_t kBytes = kOffSd + 2 * sizeof(double) * NC;  // FP64 scratch
+};
+
+template <int P>
+QL_DEV void group_reduce2(double& a, double& b) {
+#pragma unroll
+  for (int o = P / 2; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+}
+template <int P>
+QL_DEV void group_reduce2(df& a, df& b) {
+#pragma unroll
+  for (int o = P / 2; o > 0; o >>= 1) {
+    a = df_add(a, shfl_xor(a, o));
+    b = df_add(b, shfl_xor(b, o));
+  }
+}
+
+__host__ __device__ constexpr int pow2_floor(int x) { return x >= 32 ? 32 : x >= 16 ? 16 : x >= 8 ? 8 : x >= 4 ? 4 : x >= 2 ? 2 : 1; }
+
+// ---------------------------------------------------------------------------------------
+// The CTA-level factorisation state and its tile loop.
+// ---------------------------------------------------------------------------------------
+template <int NC, int TC, int RPT, int T, typename S, typename Ar>
+struct TsqrCta {
+  using Sh = TsqrShape<NC, TC, RPT, T>;
+  using Sm = TsqrSmem<NC, TC, RPT, T, S, Ar>;
+  using V = typename Ar::T;
+  static constexpr int TR = Sh::TR, NCT = Sh::NCT, B = Sh::B;
+
+  S* stage;     // [NC][B]
+  V* R;         // [NC][NC], R[j * NC + c] = R(j, c)
+  V* part;      // [NC][TR]
+  V* piv;       // [B]
+  V* fco;       // [NC]
+  int* misc;    // scalars
+  int* colmax;  // [NC] per-column max biased exponent (range check)
+  double* arena;  // aliases the stage: [Ra; Rb] during the R-tree
+  double* sd;     // FP64 scratch [2 NC]
+
+  int tid, cg, tr;
+
+  QL_DEV void init(unsigned char* smem) {
+    stage = reinterpret_cast<S*>(smem);
+    arena = reinterpret_cast<double*>(smem);
+    R = reinterpret_cast<V*>(smem + Sm::kOffR);
+    part = reinterpret_cast<V*>(smem + Sm::kOffPart);
+    piv = reinterpret_cast<V*>(smem + Sm::kOffPiv);
+    fco = reinterpret_cast<V*>(smem + Sm::kOffF);
+    misc = reinterpret_cast<int*>(smem + Sm::kOffMisc);
+    colmax = misc + 16;
+    sd = reinterpret_cast<double*>(smem + Sm::kOffSd);
+    tid = threadIdx.x;
+    cg = tid / TR;
+    tr = tid % TR;
+  }
+
+  QL_DEV void reset_r() {
+    for (int i = tid; i < NC * NC; i += T) R[i] = Ar::zero();
+    for (int i = tid; i < NC; i += T) colmax[i] = 0;
+  }
+
+  // Issue the cp.async copies of rows [row0, row0 + B) of all NC columns into the stage.
+  QL_DEV void issue_tile(const TsqrProblem<S>& p, int64_t row0) {
+    constexpr int PER = B / T > 0 ? B / T : 1;
+#pragma unroll 1
+    for (int c = 0; c < NC; ++c) {
+      const S* col = p.src.col(c < p.n ? c : 0);
+      bool cvalid = c < p.n;
+#pragma unroll
+      for (int e = 0; e < PER; ++e) {
+        int r = tid + e * T;
+        if (B % T == 0 || r < B) {
+          int64_t row = row0 + r;
+          bool v = cvalid && row < p.m;
+          cp_async_elem<S>(stage + c * B + r, v ? col + row : col, v);
+        }
+      }
+    }
+    cp_async_commit();
+  }
+
+  // Stage -> registers (with the range bookkeeping of the double-float policy).
+  QL_DEV void stage_to_regs(V (&w)[RPT][NCT]) {
+#pragma unroll
+    for (int k = 0; k < NCT; ++k) {
+      int c = cg + k * TC;
+      int emax = 0;
+#pragma unroll
+      for (int q = 0; q < RPT; ++q) {
+        int E;
+        w[q][k] = Ar::load(stage[c * B + tr + q * TR], E);
+        emax = max(emax, E);
+      }
+      if (Ar::kRangeChecked && emax > 0) atomicMax(&colmax[c], emax);
+    }
+  }
+
+  // One Householder column step j (compile-time) of the trapezoidal QR of [R; W].
+  template <int j>
+  QL_DEV void column_step(V (&w)[RPT][NCT]) {
+    // pivot column values for my rows
+    V pv[RPT];
+    if constexpr (TC == 1) {
+#pragma unroll
+      for (int q = 0; q < RPT; ++q) pv[q] = w[q][j];
+    } else {
+      if (cg == j % TC) {
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) piv[tr + q * TR] = w[q][j / TC];
+      }
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < RPT; ++q) pv[q] = piv[tr + q * TR];
+    }
+    // partial dot products W(:,j)^T W(:,c) over my rows, for my columns c >= j
+#pragma unroll
+    for (int k = 0; k < NCT; ++k) {
+      if (k * TC + TC - 1 < j) continue;  // every column of this k lies left of j
+      int c = cg + k * TC;
+      typename Ar::Acc acc = Ar::acc_zero();
+#pragma unroll
+      for (int q = 0; q < RPT; ++q) Ar::acc_fma(acc, pv[q], w[q][k]);
+      if (c >= j) part[c * TR + tr] = Ar::acc_get(acc);
+    }
+    __syncthreads();
+    // column totals and reflector coefficients: P threads per column c in [j, NC)
+    {
+      constexpr int NV = NC - j;
+      constexpr int P0 = pow2_floor(T / NV);
+      constexpr int P = P0 > TR ? pow2_floor(TR) : P0;
+      int vi = tid / P, li = tid % P;
+      bool active = vi < NV;
+      int c = j + (active ? vi : 0);
+      V d = Ar::zero(), nr = Ar::zero();
+      if (active) {
+#pragma unroll 4
+        for (int t = li; t < TR; t += P) {
+          d = Ar::add(d, part[c * TR + t]);
+          nr = Ar::add(nr, part[j * TR + t]);
+        }
+      }
+      group_reduce2<P>(d, nr);
+      if (active && li == 0) {
+        if (Ar::is_zero(nr)) {
+          fco[c] = Ar::zero();  // W(:,j) == 0: no reflector (H = I)
+          if (c == j) misc[0] = 0;
+        } else {
+          V x1 = R[j * NC + j];
+          V nrm = Ar::sqrt_(Ar::add(Ar::mul(x1, x1), nr));
+          V beta = Ar::negative(x1) ? nrm : Ar::neg(nrm);
+          V v1 = Ar::sub(x1, beta);
+          if (c == j) {
+            fco[j] = beta;  // the new diagonal, written into R after the barrier
+            misc[0] = 1;
+          } else {
+            V g = Ar::recip(Ar::neg(Ar::mul(beta, v1)));
+            V rjc = R[j * NC + c];
+            V f = Ar::mul(Ar::add(d, Ar::mul(v1, rjc)), g);
+            R[j * NC + c] = Ar::sub_mul(rjc, v1, f);
+            fco[c] = f;
+          }
+        }
+      }
+    }
+    __syncthreads();
+    if (tid == 0 && misc[0]) R[j * NC + j] = fco[j];
+    // update my columns c > j
+#pragma unroll
+    for (int k = 0; k < NCT; ++k) {
+      if (k * TC + TC - 1 <= j) continue;
+      int c = cg + k * TC;
+      if (c > j) {
+        V f = fco[c];
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) w[q][k] = Ar::sub_mul(w[q][k], pv[q], f);
+      }
+    }
+  }
+
+  // Fold the register tile into R: the in-place trapezoidal Householder QR of [R; W]
+  // (Algorithm 4, one reflector per column).
+  QL_DEV void factor_tile(V (&w)[RPT][NCT], int n) {
+    static_for<0, NC>([&](auto JC) {
+      constexpr int j = decltype(JC)::value;
+      if (j < n) column_step<j>(w);
+    });
+  }
+
+  // Process tiles [t0, t1) of problem p (tile t covers rows [row_base + t*B, ...)).
+  QL_DEV void run(const TsqrProblem<S>& p, int64_t row_base, int64_t t0, int64_t t1) {
+    V w[RPT][NCT];
+    if (t0 >= t1) return;
+    issue_tile(p, row_base + t0 * B);
+    for (int64_t t = t0; t < t1; ++t) {
+      cp_async_wait_all();
+      __syncthreads();
+      stage_to_regs(w);
+      __syncthreads();
+      if (t + 1 < t1) issue_tile(p, row_base + (t + 1) * B);
+      factor_tile(w, p.n);
+    }
+    __syncthreads();
+  }
+
+  // Range verdict of this CTA (double-float policy): every nonzero column max exponent
+  // must lie in [kDfEminLimit, kDfEmaxLimit].
+  QL_DEV bool out_of_range(int n) {
+    if constexpr (!Ar::kRangeChecked) return false;
+    bool bad = false;
+    for (int c = 0; c < n; ++c) {
+      int e = colmax[c];
+      if (e != 0 && (e < kDfEminLimit || e > kDfEmaxLimit)) bad = true;
+    }
+    return bad;
+  }
+};
+
+// ---------------------------------------------------------------------------------------
+// FP64 merge of two triangles [Ra; Rb] -> Ra (n x n each, in shared memory, ld NC).
+// Column j's reflector touches Ra(j, :) and Rb(0..j, :) (Rb stays upper triangular in
+// its untouched part).  T threads, one column each per step.
+// ---------------------------------------------------------------------------------------
+template <int NC, int T>
+QL_DEV void merge_pair_f64(double* Ra, double* Rb, int n, double* sd) {
+  int tid = threadIdx.x;
+  for (int j = 0; j < n; ++j) {
+    double x1 = Ra[j * NC + j];
+    for (int c = j + tid; c < n; c += T) {
+      double s = 0.0;
+      for (int i = 0; i <= j; ++i) s = fma(Rb[i * NC + j], Rb[i * NC + c], s);
+      sd[c] = s;
+    }
+    __syncthreads();
+    double nr = sd[j];
+    if (nr != 0.0) {
+      double nrm = sqrt(fma(x1, x1, nr));
+      double beta = x1 < 0.0 ? nrm : -nrm;
+      double v1 = x1 - beta;
+      double g = -1.0 / (beta * v1);
+      for (int c = j + 1 + tid; c < n; c += T) {
+        double f = fma(v1, Ra[j * NC + c], sd[c]) * g;
+        Ra[j * NC + c] = fma(-v1, f, Ra[j * NC + c]);
+        for (int i = 0; i <= j; ++i) Rb[i * NC + c] = fma(-Rb[i * NC + j], f, Rb[i * NC + c]);
+      }
+      if (tid == 0) Ra[j * NC + j] = beta;
+    }
+    __syncthreads();
+  }
+}
+
+// Copy an n x n triangle from global (ld n) into shared (ld NC), zero-padded to NC.
+template <int NC, int T>
+QL_DEV void load_tri(double* dst, const double* src, int n) {
+  for (int i = threadIdx.x; i < NC * NC; i += T) {
+    int r = i / NC, c = i % NC;
+    dst[i] = (r < n && c < n && r <= c) ? __ldcg(src + (size_t)c * n + r) : 0.0;
+  }
+}
+template <int NC, int T>
+QL_DEV void store_tri(double* dst, const double* src, int n) {
+  for (int i = threadIdx.x; i < n * n; i += T) {
+    int c = i / n, r = i % n;
+    __stcg(dst + i, r <= c ? src[r * NC + c] : 0.0);
+  }
+}
+
+// Climb the binary R-tree from leaf `leaf` whose triangle is already in slot(0, leaf).
+// Returns true in exactly one CTA (the root owner), with the final triangle in Ra (smem,
+// ld NC).  Slots of level l start at sum_{l' < l} width_l'; counters likewise.
+template <int NC, int T>
+QL_DEV bool climb_tree(const TreeView& tv, int leaf, int n, double* Ra, double* Rb, double* sd, int* s_flag) {
+  int width = tv.leaves, idx = leaf;
+  size_t slot_base = 0, cnt_base = 0;
+  if (width == 1) {
+    load_tri<NC, T>(Ra, tv.slots, n);
+    __syncthreads();
+    return true;
+  }
+  while (width > 1) {
+    int parent = idx >> 1;
+    bool pair = (2 * parent + 1) < width;
+    size_t next_slot_base = slot_base + width;
+    int next_width = (width + 1) >> 1;
+    double* my_slot = tv.slots + (slot_base + (size_t)idx) * (size_t)n * n;
+    if (pair) {
+      __threadfence();
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        int old = atomicAdd(&tv.counters[cnt_base + parent], 1);
+        *s_flag = old;
+        if (old == 1) tv.counters[cnt_base + parent] = 0;  // reset for the next call
+      }
+      __syncthreads();
+      if (*s_flag == 0) return false;  // sibling merges
+      __threadfence();
+      const double* a = tv.slots + (slot_base + 2 * (size_t)parent) * (size_t)n * n;
+      const double* b = a + (size_t)n * n;
+      load_tri<NC, T>(Ra, a, n);
+      load_tri<NC, T>(Rb, b, n);
+      __syncthreads();
+      merge_pair_f64<NC, T>(Ra, Rb, n, sd);
+    } else {
+      load_tri<NC, T>(Ra, my_slot, n);
+      __syncthreads();
+    }
+    cnt_base += (size_t)(width >> 1);
+    slot_base = next_slot_base;
+    width = next_width;
+    idx = parent;
+    if (width > 1) {
+      store_tri<NC, T>(tv.slots + (slot_base + (size_t)idx) * (size_t)n * n, Ra, n);
+      __syncthreads();
+    }
+  }
+  return true;
+}
+
+// Tree sizes for `leaves` leaves: total slots and counters.
+inline size_t tree_slots(int leaves) {
+  size_t s = 0;
+  for (int w = leaves; ; w = (w + 1) >> 1) {
+    s += (size_t)w;
+    if (w <= 1) break;
+  }
+  return s;
+}
+inline size_t tree_counters(int leaves) {
+  size_t s = 0;
+  for (int w = leaves; w > 1; w = (w + 1) >> 1) s += (size_t)(w >> 1);
+  return s + 1;
+}
+
+}  // namespace ql
