@@ -87,26 +87,23 @@ QL_DEV df df_from_double_rn(double x) {  // used only on n x n data
   return df{hi, lo};
 }
 
-// Split an IEEE double into a double-float with integer operations only (the FP64 pipe is
-// the scarce resource on this GPU): hi = the top 24 significand bits, lo = the next 23,
-// both truncated, so |x - (hi + lo)| < 2^-47 |x|.  Zero and subnormals give 0.
-// The biased exponent E of x is returned for the range check.
+// Split an IEEE double into a double-float without the FP64 pipe (the scarce resource on
+// this GPU): hi = the top 24 significand bits (truncated, built with integer operations),
+// lo = the remaining 29 bits converted to float with rounding, so |x - (hi + lo)| <=
+// 2^-48 |x|.  Doubles outside [2^-103, 2^127) give 0 (the range check rejects them); the
+// biased exponent E of x is returned for that check.
 QL_DEV df df_split_double(double x, int& E) {
   unsigned long long bits = (unsigned long long)__double_as_longlong(x);
   unsigned int hw = (unsigned int)(bits >> 32), lw = (unsigned int)bits;
   unsigned int sign = hw & 0x80000000u;
   E = (int)((hw >> 20) & 0x7ffu);
-  if (E < 920 || E > 1150) {  // out of the double-float range (zero included): flag via E
-    df z{0.0f, 0.0f};
-    if (E > 1150 && E < 2047) z.hi = __int_as_float((int)(sign | 0x7f000000u));  // huge: keep order
-    return z;
-  }
+  if (E < 920 || E > 1150) return df{0.0f, 0.0f};
   unsigned int hb = sign | ((unsigned int)(E - 896) << 23) | ((hw & 0xfffffu) << 3) | (lw >> 29);
-  unsigned int eb = sign | ((unsigned int)(E - 919) << 23);
-  unsigned int lb = eb | ((lw >> 6) & 0x7fffffu);
+  float scale = __int_as_float((int)((unsigned int)(E - 919) << 23));  // 2^(E - 1046)
+  float lo = __fmul_rn(__fmul_rn(__uint2float_rn(lw & 0x1fffffffu), 1.862645149230957e-09f), scale);
   df r;
   r.hi = __int_as_float((int)hb);
-  r.lo = __fsub_rn(__int_as_float((int)lb), __int_as_float((int)eb));
+  r.lo = sign ? -lo : lo;
   return r;
 }
 
@@ -154,6 +151,8 @@ struct ArithDF {
   QL_DEV static T neg(T a) { return df_neg(a); }
   QL_DEV static bool is_zero(T a) { return a.hi == 0.0f; }
   QL_DEV static bool negative(T a) { return a.hi < 0.0f; }
+  QL_DEV static bool le(T a, T b) { return a.hi <= b.hi; }  // approximate order suffices
+  QL_DEV static T tau2() { return df{0x1p-80f, 0.0f}; }      // (2^-40)^2: negligible remainder
   QL_DEV static double to_double(T a) { return df_to_double(a); }
   QL_DEV static T from_double(double x) { return df_from_double_rn(x); }
   QL_DEV static T shfl(T a, int mask) { return shfl_xor(a, mask); }
@@ -184,6 +183,8 @@ struct ArithF64 {
   QL_DEV static T neg(T a) { return -a; }
   QL_DEV static bool is_zero(T a) { return a == 0.0; }
   QL_DEV static bool negative(T a) { return a < 0.0; }
+  QL_DEV static bool le(T a, T b) { return a <= b; }
+  QL_DEV static T tau2() { return 0x1p-92; }  // (2^-46)^2: negligible remainder
   QL_DEV static double to_double(T a) { return a; }
   QL_DEV static T from_double(double x) { return x; }
   QL_DEV static T shfl(T a, int mask) { return __shfl_xor_sync(0xffffffffu, a, mask); }

@@ -170,6 +170,9 @@ QL_DEV int jacobi_eig(double* A, int ld, double* U, int ldu, int n, double* sc, 
 // triangle of Z holds R (beta = -sign(x_1) ||x|| convention, zero columns skipped).
 template <int T>
 QL_DEV void householder_square(double* Z, int ld, int n, double* sd) {
+  double* cnm = sd + n;  // sum over finished rows i < j of Z(i, c)^2
+  for (int c = threadIdx.x; c < n; c += T) cnm[c] = 0.0;
+  __syncthreads();
   for (int j = 0; j < n; ++j) {
     for (int c = j + threadIdx.x; c < n; c += T) {
       double s = 0.0;
@@ -179,17 +182,23 @@ QL_DEV void householder_square(double* Z, int ld, int n, double* sd) {
     double x1 = Z[j * ld + j];
     __syncthreads();
     double nr = sd[j];
-    if (nr != 0.0) {
-      double nrm = sqrt(fma(x1, x1, nr));
+    double rem = fma(x1, x1, nr);
+    bool skip = nr == 0.0 || rem <= 0x1p-92 * (cnm[j] + rem);  // residue below 2^-46 of the column
+    if (!skip) {
+      double nrm = sqrt(rem);
       double beta = x1 < 0.0 ? nrm : -nrm;
       double v1 = x1 - beta;
       double g = -1.0 / (beta * v1);
       for (int c = j + 1 + threadIdx.x; c < n; c += T) {
         double f = fma(v1, Z[j * ld + c], sd[c]) * g;
-        Z[j * ld + c] = fma(-v1, f, Z[j * ld + c]);
+        double rn = fma(-v1, f, Z[j * ld + c]);
+        Z[j * ld + c] = rn;
+        cnm[c] = fma(rn, rn, cnm[c]);
         for (int i = j + 1; i < n; ++i) Z[i * ld + c] = fma(-Z[i * ld + j], f, Z[i * ld + c]);
       }
       if (threadIdx.x == 0) Z[j * ld + j] = beta;
+    } else {
+      for (int c = j + 1 + threadIdx.x; c < n; c += T) cnm[c] = fma(Z[j * ld + c], Z[j * ld + c], cnm[c]);
     }
     __syncthreads();
   }

@@ -61,7 +61,8 @@ struct TsqrSmem {
   static constexpr size_t kOffPart = kOffR + kR;
   static constexpr size_t kOffPiv = kOffPart + kPart;
   static constexpr size_t kOffF = kOffPiv + kPiv;
-  static constexpr size_t kOffMisc = kOffF + kF;                     // int[16] + int[NC]
+  static constexpr size_t kOffCn = kOffF + kF;                       // running column norms
+  static constexpr size_t kOffMisc = kOffCn + sizeof(V) * NC;        // int[16] + int[NC]
   static constexpr size_t kOffSd = (kOffMisc + (16 + NC) * sizeof(int) + 15) / 16 * 16;
   static constexpr size_t kBytes = kOffSd + 2 * sizeof(double) * NC;  // FP64 scratch
 };
@@ -100,6 +101,7 @@ struct TsqrCta {
   V* part;      // [NC][TR]
   V* piv;       // [B]
   V* fco;       // [NC]
+  V* cn;        // [NC] sum over finished rows i < j of R(i, c)^2 within the current tile
   int* misc;    // scalars
   int* colmax;  // [NC] per-column max biased exponent (range check)
   double* arena;  // aliases the stage: [Ra; Rb] during the R-tree
@@ -114,6 +116,7 @@ struct TsqrCta {
     part = reinterpret_cast<V*>(smem + Sm::kOffPart);
     piv = reinterpret_cast<V*>(smem + Sm::kOffPiv);
     fco = reinterpret_cast<V*>(smem + Sm::kOffF);
+    cn = reinterpret_cast<V*>(smem + Sm::kOffCn);
     misc = reinterpret_cast<int*>(smem + Sm::kOffMisc);
     colmax = misc + 16;
     sd = reinterpret_cast<double*>(smem + Sm::kOffSd);
@@ -147,34 +150,60 @@ struct TsqrCta {
     cp_async_commit();
   }
 
-  // Stage -> registers (with the range bookkeeping of the double-float policy).
+  // Stage -> registers (with the range bookkeeping of the double-float policy: the
+  // column's largest exponent is reduced over the lanes that share the column, then one
+  // shared-memory atomic per column and warp records it).
   QL_DEV void stage_to_regs(V (&w)[RPT][NCT]) {
+    constexpr unsigned kHalf = TR >= 32 ? 0xffffffffu : 0x0000ffffu;
+    const unsigned gmask = TR >= 32 ? 0xffffffffu : (((tid & 31) < 16) ? kHalf : (kHalf << 16));
 #pragma unroll
     for (int k = 0; k < NCT; ++k) {
       int c = cg + k * TC;
-      int emax = 0;
+      unsigned emax = 0;
 #pragma unroll
       for (int q = 0; q < RPT; ++q) {
         int E;
         w[q][k] = Ar::load(stage[c * B + tr + q * TR], E);
-        emax = max(emax, E);
+        emax = max(emax, (unsigned)E);
       }
-      if (Ar::kRangeChecked && emax > 0) atomicMax(&colmax[c], emax);
+      if constexpr (Ar::kRangeChecked) {
+        emax = __reduce_max_sync(gmask, emax);
+        if ((tid & (TR >= 32 ? 31 : 15)) == 0 && emax > 0) atomicMax(&colmax[c], (int)emax);
+      }
     }
   }
 
-  // One Householder column step j (compile-time) of the trapezoidal QR of [R; W].
-  template <int j>
-  QL_DEV void column_step(V (&w)[RPT][NCT]) {
-    // pivot column values for my rows
+  // Group reduction of two values over P consecutive lanes (P a power of two <= 32).
+  QL_DEV static void group_reduce_rt(V& a, V& b, int P) {
+    for (int o = P >> 1; o > 0; o >>= 1) {
+      a = Ar::add(a, Ar::shfl(a, o));
+      b = Ar::add(b, Ar::shfl(b, o));
+    }
+  }
+
+  // One Householder column step j of the trapezoidal QR of [R; W].  The loop over j is
+  // not unrolled (the unrolled form overflows the instruction cache); register indices
+  // stay compile-time: every local column k is processed under a warp-uniform test on j.
+  QL_DEV void column_step(V (&w)[RPT][NCT], int j) {
+    const int kj = j / TC;  // local index of column j in its owner group
     V pv[RPT];
     if constexpr (TC == 1) {
 #pragma unroll
-      for (int q = 0; q < RPT; ++q) pv[q] = w[q][j];
+      for (int q = 0; q < RPT; ++q) pv[q] = w[q][0];
+#pragma unroll
+      for (int k = 1; k < NCT; ++k)
+        if (kj == k) {
+#pragma unroll
+          for (int q = 0; q < RPT; ++q) pv[q] = w[q][k];
+        }
     } else {
       if (cg == j % TC) {
 #pragma unroll
-        for (int q = 0; q < RPT; ++q) piv[tr + q * TR] = w[q][j / TC];
+        for (int k = 0; k < NCT; ++k)
+          if (kj == k) {
+#pragma unroll
+            for (int q = 0; q < RPT; ++q) piv[tr + q * TR] = w[q][k];
+          }
       }
       __syncthreads();
 #pragma unroll
@@ -183,38 +212,47 @@ struct TsqrCta {
     // partial dot products W(:,j)^T W(:,c) over my rows, for my columns c >= j
 #pragma unroll
     for (int k = 0; k < NCT; ++k) {
-      if (k * TC + TC - 1 < j) continue;  // every column of this k lies left of j
-      int c = cg + k * TC;
-      typename Ar::Acc acc = Ar::acc_zero();
+      const int c = cg + k * TC;
+      if (c >= j) {
+        typename Ar::Acc acc = Ar::acc_zero();
 #pragma unroll
-      for (int q = 0; q < RPT; ++q) Ar::acc_fma(acc, pv[q], w[q][k]);
-      if (c >= j) part[c * TR + tr] = Ar::acc_get(acc);
+        for (int q = 0; q < RPT; ++q) Ar::acc_fma(acc, pv[q], w[q][k]);
+        part[c * TR + tr] = Ar::acc_get(acc);
+      }
     }
     __syncthreads();
     // column totals and reflector coefficients: P threads per column c in [j, NC)
     {
-      constexpr int NV = NC - j;
-      constexpr int P0 = pow2_floor(T / NV);
-      constexpr int P = P0 > TR ? pow2_floor(TR) : P0;
-      int vi = tid / P, li = tid % P;
-      bool active = vi < NV;
-      int c = j + (active ? vi : 0);
+      const int NV = NC - j;
+      int P = pow2_floor(T / NV);
+      if (P > TR) P = pow2_floor(TR);
+      const int vi = tid / P, li = tid % P;
+      const bool active = vi < NV;
+      const int c = j + (active ? vi : 0);
       V d = Ar::zero(), nr = Ar::zero();
       if (active) {
-#pragma unroll 4
         for (int t = li; t < TR; t += P) {
           d = Ar::add(d, part[c * TR + t]);
           nr = Ar::add(nr, part[j * TR + t]);
         }
       }
-      group_reduce2<P>(d, nr);
+      group_reduce_rt(d, nr, P);
       if (active && li == 0) {
-        if (Ar::is_zero(nr)) {
-          fco[c] = Ar::zero();  // W(:,j) == 0: no reflector (H = I)
+        // Householder preserves the 2-norm of column j of [R; W]: cn[j] + x1^2 + nr is its
+        // norm at the start of the tile.  A remainder below kTau of it is rounding residue
+        // (a tile with fewer independent rows than columns): no reflector is built from it.
+        V x1 = R[j * NC + j];
+        V rem = Ar::add(Ar::mul(x1, x1), nr);
+        bool skip = Ar::is_zero(nr) || Ar::le(rem, Ar::mul(Ar::add(cn[j], rem), Ar::tau2()));
+        if (skip) {
+          fco[c] = Ar::zero();  // H = I
           if (c == j) misc[0] = 0;
+          if (c > j) {
+            V rjc = R[j * NC + c];
+            cn[c] = Ar::add(cn[c], Ar::mul(rjc, rjc));
+          }
         } else {
-          V x1 = R[j * NC + j];
-          V nrm = Ar::sqrt_(Ar::add(Ar::mul(x1, x1), nr));
+          V nrm = Ar::sqrt_(rem);
           V beta = Ar::negative(x1) ? nrm : Ar::neg(nrm);
           V v1 = Ar::sub(x1, beta);
           if (c == j) {
@@ -224,7 +262,9 @@ struct TsqrCta {
             V g = Ar::recip(Ar::neg(Ar::mul(beta, v1)));
             V rjc = R[j * NC + c];
             V f = Ar::mul(Ar::add(d, Ar::mul(v1, rjc)), g);
-            R[j * NC + c] = Ar::sub_mul(rjc, v1, f);
+            V rn = Ar::sub_mul(rjc, v1, f);
+            R[j * NC + c] = rn;
+            cn[c] = Ar::add(cn[c], Ar::mul(rn, rn));
             fco[c] = f;
           }
         }
@@ -235,8 +275,7 @@ struct TsqrCta {
     // update my columns c > j
 #pragma unroll
     for (int k = 0; k < NCT; ++k) {
-      if (k * TC + TC - 1 <= j) continue;
-      int c = cg + k * TC;
+      const int c = cg + k * TC;
       if (c > j) {
         V f = fco[c];
 #pragma unroll
@@ -248,10 +287,8 @@ struct TsqrCta {
   // Fold the register tile into R: the in-place trapezoidal Householder QR of [R; W]
   // (Algorithm 4, one reflector per column).
   QL_DEV void factor_tile(V (&w)[RPT][NCT], int n) {
-    static_for<0, NC>([&](auto JC) {
-      constexpr int j = decltype(JC)::value;
-      if (j < n) column_step<j>(w);
-    });
+#pragma unroll 1
+    for (int j = 0; j < n; ++j) column_step(w, j);
   }
 
   // Process tiles [t0, t1) of problem p (tile t covers rows [row_base + t*B, ...)).
@@ -263,6 +300,7 @@ struct TsqrCta {
       cp_async_wait_all();
       __syncthreads();
       stage_to_regs(w);
+      for (int i = tid; i < NC; i += T) cn[i] = Ar::zero();
       __syncthreads();
       if (t + 1 < t1) issue_tile(p, row_base + (t + 1) * B);
       factor_tile(w, p.n);
@@ -288,9 +326,16 @@ struct TsqrCta {
 // Column j's reflector touches Ra(j, :) and Rb(0..j, :) (Rb stays upper triangular in
 // its untouched part).  T threads, one column each per step.
 // ---------------------------------------------------------------------------------------
+// Remainders below kTauF64 of their column's norm are treated as rounding residue (no
+// reflector), as in the tile factorisation.
+constexpr double kTauF64Sq = 0x1p-92;  // (2^-46)^2
+
 template <int NC, int T>
 QL_DEV void merge_pair_f64(double* Ra, double* Rb, int n, double* sd) {
   int tid = threadIdx.x;
+  double* cnm = sd + NC;  // sum over finished rows i < j of Ra(i, c)^2
+  for (int c = tid; c < NC; c += T) cnm[c] = 0.0;
+  __syncthreads();
   for (int j = 0; j < n; ++j) {
     double x1 = Ra[j * NC + j];
     for (int c = j + tid; c < n; c += T) {
@@ -300,17 +345,23 @@ QL_DEV void merge_pair_f64(double* Ra, double* Rb, int n, double* sd) {
     }
     __syncthreads();
     double nr = sd[j];
-    if (nr != 0.0) {
-      double nrm = sqrt(fma(x1, x1, nr));
+    double rem = fma(x1, x1, nr);
+    bool skip = nr == 0.0 || rem <= kTauF64Sq * (cnm[j] + rem);
+    if (!skip) {
+      double nrm = sqrt(rem);
       double beta = x1 < 0.0 ? nrm : -nrm;
       double v1 = x1 - beta;
       double g = -1.0 / (beta * v1);
       for (int c = j + 1 + tid; c < n; c += T) {
         double f = fma(v1, Ra[j * NC + c], sd[c]) * g;
-        Ra[j * NC + c] = fma(-v1, f, Ra[j * NC + c]);
+        double rn = fma(-v1, f, Ra[j * NC + c]);
+        Ra[j * NC + c] = rn;
+        cnm[c] = fma(rn, rn, cnm[c]);
         for (int i = 0; i <= j; ++i) Rb[i * NC + c] = fma(-Rb[i * NC + j], f, Rb[i * NC + c]);
       }
       if (tid == 0) Ra[j * NC + j] = beta;
+    } else {
+      for (int c = j + 1 + tid; c < n; c += T) cnm[c] = fma(Ra[j * NC + c], Ra[j * NC + c], cnm[c]);
     }
     __syncthreads();
   }
@@ -337,6 +388,7 @@ QL_DEV void store_tri(double* dst, const double* src, int n) {
 // ld NC).  Slots of level l start at sum_{l' < l} width_l'; counters likewise.
 template <int NC, int T>
 QL_DEV bool climb_tree(const TreeView& tv, int leaf, int n, double* Ra, double* Rb, double* sd, int* s_flag) {
+  __syncthreads();  // the leaf slot was written by all threads of this CTA
   int width = tv.leaves, idx = leaf;
   size_t slot_base = 0, cnt_base = 0;
   if (width == 1) {
