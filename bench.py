@@ -1,0 +1,381 @@
+"""Benchmark of the Q-less QR hot path on GB300 (one JSON line on stdout, rank 0).
+
+Workload (one "step"): the single-matrix condition sweep -- X = G S with m = 2^25 rows,
+n in {1, 2, 4, 8, 16, 32, 64}, kappa = 1e4, FP64 storage, each X factored by Q-less TSQR,
+Cholesky-QR2 and SVQB2.  Inputs are device-resident before the timed region and every X is
+larger than the 129 MB L2 (>= 268 MB), so no L2 flush is needed between steps.
+
+metric: effective GB/s = sum over calls of 8 m n bytes / sum of the calls' time (the
+paper's "effective bandwidth", counted once per call even though the Gram methods read X
+twice).  Per-call breakdown, the roofline of the dominant kernel, the oracle on the host
+cores, the host-buffer end-to-end number and the SM clocks seen during the timed region
+are attached.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+N > 1 runs under torch.distributed.run: every rank factors the same sweep on its own GPU
+(independent replicas; the method has no cross-GPU exchange in this build).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+M = 1 << 25
+NS = [1, 2, 4, 8, 16, 32, 64]
+KAPPA = 1e4
+METHODS = ["tsqr", "cholqr2", "svqb2"]
+PASSES = {"tsqr": 1, "cholqr2": 2, "svqb2": 2}
+METRIC = "Q-less QR effective GB/s (8mn B/time)"
+WORKLOAD = ("Q-less QR condition sweep: X = G S, m = 2^25 rows, n in {1,2,4,8,16,32,64}, kappa = 1e4, "
+            "FP64 storage; TSQR + Cholesky-QR2 + SVQB2 per n")
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    return p.parse_args()
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() in ("active", "0x1", "1"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ our arm
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    import paper_2603_20889_gb300 as q
+    from paper_2603_20889_gb300 import synth
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    lib = q.load_library()
+    stream = torch.cuda.current_stream()
+    sptr = q._stream_ptr(stream)
+
+    # inputs resident in HBM before the timed region
+    Xs = {n: synth.conditioned_device(M, n, KAPPA, seed=1000 + n, device=dev) for n in NS}
+    nmax = max(NS)
+    wsb = max(lib.ql_workspace_bytes(q.QL_AUTO, M, n, q.QL_F64) for n in NS)
+    ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    Rb = {n: torch.empty((n, n), dtype=torch.float64, device=dev) for n in NS}
+    info = torch.zeros((len(NS) * len(METHODS), 2), dtype=torch.int32, device=dev)
+
+    def call(method, n, X, R, inf):
+        ptr = X.data_ptr()
+        if method == "tsqr":
+            st = lib.ql_tsqr_qless(M, n, ptr, q.QL_F64, M, R.data_ptr(), n, inf.data_ptr(), ws.data_ptr(), wsb, sptr)
+        elif method == "cholqr2":
+            st = lib.ql_cholqr2_qless(M, n, ptr, q.QL_F64, M, R.data_ptr(), n, inf.data_ptr(), ws.data_ptr(), wsb,
+                                      sptr)
+        else:
+            st = lib.ql_svqb_qless(M, n, ptr, q.QL_F64, M, R.data_ptr(), n, None, 0.0, inf.data_ptr(),
+                                   ws.data_ptr(), wsb, sptr)
+        if st != 0:
+            raise RuntimeError(f"{method} n={n}: status {st}")
+
+    calls = [(meth, n) for n in NS for meth in METHODS]
+    evs = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in calls]
+           for _ in range(args.steps)]
+
+    def step(ev=None):
+        for i, (meth, n) in enumerate(calls):
+            if ev:
+                ev[i][0].record(stream)
+            call(meth, n, Xs[n], Rb[n], info[i])
+            if ev:
+                ev[i][1].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    bad = [(calls[i], v) for i, v in enumerate(info.cpu().tolist()) if v[0] != 0]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    time.sleep(0.3)
+    per_call = [0.0] * len(calls)
+    l0 = lib.ql_launch_count()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for k in range(args.steps):
+        step(evs[k])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    for k in range(args.steps):  # per-call device times (events on the launching stream)
+        for i in range(len(calls)):
+            per_call[i] += evs[k][i][0].elapsed_time(evs[k][i][1])
+    launches = lib.ql_launch_count() - l0
+    if world > 1:
+        torch.distributed.barrier()
+    total_ms = t_start.elapsed_time(t_end)
+    clk = clocks.stop()
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+
+    bytes_step = sum(8.0 * M * n for (_, n) in calls)
+    ms_step = total_ms / args.steps
+    value = world * bytes_step * args.steps / (total_ms / 1e3) / 1e9
+
+    # dominant call (largest share of the step) and its roofline (HBM, algorithmic bytes)
+    peak, peak_kind = measured_peaks()
+    sweep = []
+    for i, (meth, n) in enumerate(calls):
+        ms = per_call[i] / args.steps
+        sweep.append({"method": meth, "n": n, "ms": round(ms, 4), "eff_gbs": round(8.0 * M * n / ms / 1e6, 1),
+                      "alg_gbs": round(PASSES[meth] * 8.0 * M * n / ms / 1e6, 1)})
+    dom = max(range(len(calls)), key=lambda i: per_call[i])
+    dmeth, dn = calls[dom]
+    dms = per_call[dom] / args.steps
+    launches_per_call = 2 if dmeth == "tsqr" else 4  # kernels incl. the gated FP64 launches
+    # the timed share of the dominant kernel: one pass = one launch reading 8 m n bytes
+    kern_ms = dms / PASSES[dmeth]
+    achieved = 8.0 * M * dn / kern_ms / 1e6
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": None, "peak_source": peak_kind,
+                "kernel": f"{'tsqr_kernel' if dmeth == 'tsqr' else 'gram_kernel'} ({dmeth}, n={dn}, m=2^25)",
+                "algorithmic_bytes_per_launch": 8 * M * dn,
+                "note": "per-launch time from CUDA events around the call on its stream; Gram methods: "
+                        "call time / 2 passes"}
+
+    e2e = run_e2e(args, q, lib, torch, dev, Xs, ws, wsb, stream) if args.e2e_steps > 0 else None
+    out = {
+        "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32x2", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "storage": "f64", "arith": "double-float (f32x2) m-loops, FP64 n x n",
+                   "m": M, "n": NS, "kappa": KAPPA, "methods": METHODS, "parallelism": f"replicas x{world}",
+                   "l2": "every input > L2 (>= 268 MB); no flush needed"},
+        "roofline": roofline, "clocks": clk, "gpu_launches": int(launches),
+        "gpu_launches_per_step": int(launches) // max(args.steps, 1),
+        "sweep": sweep, "status_errors": bad,
+    }
+    if e2e:
+        out["e2e"] = e2e
+    return out
+
+
+def run_e2e(args, q, lib, torch, dev, Xs, ws, wsb, stream):
+    """The same sweep through the C ABI from HOST buffers: every step copies each X from
+    pinned host memory to the device and reads every R back, inside the timed region."""
+    import torch as _t
+
+    host = {n: _t.empty(Xs[n].shape, dtype=Xs[n].dtype, pin_memory=True) for n in NS}
+    for n in NS:
+        host[n].copy_(Xs[n])
+    dbuf = {n: _t.empty_like(Xs[n]) for n in NS}
+    Rh = {n: _t.empty((n, n), dtype=_t.float64, pin_memory=True) for n in NS}
+    Rd = {n: _t.empty((n, n), dtype=_t.float64, device=dev) for n in NS}
+    inf = _t.zeros(2, dtype=_t.int32, device=dev)
+    sptr = q._stream_ptr(stream)
+    h2d = sum(host[n].numel() * 8 for n in NS)
+    d2h = sum(Rh[n].numel() * 8 * len(METHODS) for n in NS)
+
+    def step():
+        for n in NS:
+            dbuf[n].copy_(host[n], non_blocking=True)
+            X = dbuf[n].data_ptr()
+            for meth in METHODS:
+                if meth == "tsqr":
+                    lib.ql_tsqr_qless(M, n, X, q.QL_F64, M, Rd[n].data_ptr(), n, inf.data_ptr(), ws.data_ptr(), wsb, sptr)
+                elif meth == "cholqr2":
+                    lib.ql_cholqr2_qless(M, n, X, q.QL_F64, M, Rd[n].data_ptr(), n, inf.data_ptr(), ws.data_ptr(),
+                                         wsb, sptr)
+                else:
+                    lib.ql_svqb_qless(M, n, X, q.QL_F64, M, Rd[n].data_ptr(), n, None, 0.0, inf.data_ptr(),
+                                      ws.data_ptr(), wsb, sptr)
+                Rh[n].copy_(Rd[n], non_blocking=True)
+
+    step()
+    _t.cuda.synchronize()
+    e0, e1 = _t.cuda.Event(enable_timing=True), _t.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.e2e_steps):
+        step()
+    e1.record(stream)
+    _t.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.e2e_steps
+    bytes_step = sum(8.0 * M * n * len(METHODS) for n in NS)
+    del host, dbuf
+    return {"value": round(bytes_step / (ms / 1e3) / 1e9, 2), "unit": "GB/s", "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": round(ms, 3),
+            "note": "each X copied host->device once per step (pinned), R read back after every call"}
+
+
+# ------------------------------------------------------------------ the oracle on the host
+
+
+def oracle_sample(seconds: float):
+    """Time the CPU oracle (plain Householder, long-double accumulation, one thread) on a
+    bounded row sample of the same sweep; returns (GB/s in the metric's unit, detail)."""
+    import numpy as np
+
+    import oracle
+    from paper_2603_20889_gb300 import synth
+
+    # calibrate: rows per second at n = 8
+    Xc = synth.conditioned(20000, 8, KAPPA, seed=7)
+    t0 = time.perf_counter()
+    oracle.householder_r(Xc)
+    dt = max(time.perf_counter() - t0, 1e-4)
+    flop_rate = 2.0 * 20000 * 64 / dt  # oracle Householder flops per second
+    budget = seconds / (len(NS) * len(METHODS))
+    total_bytes, total_s, parts = 0.0, 0.0, []
+    for n in NS:
+        ms_rows = int(max(256, min(M, budget * flop_rate / (2.0 * n * n))))
+        X = synth.conditioned(ms_rows, n, KAPPA, seed=1000 + n)
+        for meth in METHODS:
+            t0 = time.perf_counter()
+            if meth == "tsqr":
+                oracle.householder_r(X)
+            elif meth == "cholqr2":
+                oracle.cholqr2(X)
+            else:
+                oracle.svqb2(X)
+            s = time.perf_counter() - t0
+            total_s += s
+            total_bytes += 8.0 * ms_rows * n
+            parts.append(f"{meth} n={n} m={ms_rows}")
+    return total_bytes / total_s / 1e9, total_s, "; ".join(parts)
+
+
+def cpu_baseline(seconds):
+    v, s, sample = oracle_sample(seconds)
+    return {"value": round(v, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"row samples of the same sweep ({s:.1f} s of CPU): {sample}"}
+
+
+# ------------------------------------------------------------------ main
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        per_step = []
+        for _ in range(args.warmup):
+            oracle_sample(min(args.cpu_seconds, 4.0) / 4)
+        for _ in range(args.steps):
+            v, s, sample = oracle_sample(args.cpu_seconds / max(args.steps, 1))
+            per_step.append((v, s))
+        value = statistics.median(v for v, _ in per_step)
+        ms = statistics.mean(s for _, s in per_step) * 1e3
+        print(json.dumps({
+            "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "GB/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": "bounded row samples per step (the oracle is a CPU program)"},
+            "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(value, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }))
+        return 0
+    if world > 1:
+        import torch
+
+        torch.distributed.init_process_group("nccl")
+    out = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        out["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+        print(json.dumps(out))
+    if world > 1:
+        import torch
+
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -78,6 +78,10 @@ ql_arith ql_set_arith(ql_arith mode);
 /* Library version and build identity, e.g. "qless 0.1 sm_103a". Static string. */
 const char* ql_version(void);
 
+/* Number of kernels this library has launched in this process (instrumentation for
+ * benchmarks: every launch of every entry point, gated fallback launches included). */
+uint64_t ql_launch_count(void);
+
 /* Device workspace bytes for one call of `method` on an m x n problem of `dtype`
  * (QL_AUTO: the maximum over the methods).  0 on bad arguments. */
 size_t ql_workspace_bytes(ql_method method, int64_t m, int64_t n, ql_dtype dtype);

@@ -35,6 +35,7 @@ _i64, _i32, _vp, _dp, _sz, _f64 = ctypes.c_int64, ctypes.c_int32, ctypes.c_void_
 SIGNATURES = {
     "ql_set_arith": (_i32, [_i32]),
     "ql_version": (ctypes.c_char_p, []),
+    "ql_launch_count": (ctypes.c_uint64, []),
     "ql_workspace_bytes": (_sz, [_i32, _i64, _i64, _i32]),
     "ql_tsqr_qless": (_i32, [_i64, _i64, _vp, _i32, _i64, _dp, _i64, _vp, _vp, _sz, _vp]),
     "ql_cholqr2_qless": (_i32, [_i64, _i64, _vp, _i32, _i64, _dp, _i64, _vp, _vp, _sz, _vp]),

@@ -11,6 +11,8 @@ namespace ql {
 constexpr int kApiMaxN = 64;  // largest n any entry point accepts
 
 static std::atomic<int> g_arith{QL_ARITH_DF};
+static std::atomic<unsigned long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 ql_arith current_arith() { return (ql_arith)g_arith.load(); }
 
 static bool elem_aligned(const void* p, ql_dtype dt) {
@@ -39,6 +41,8 @@ ql_arith ql_set_arith(ql_arith mode) {
 }
 
 const char* ql_version(void) { return "qless 0.1 sm_103a"; }
+
+uint64_t ql_launch_count(void) { return g_launches.load(); }
 
 size_t ql_workspace_bytes(ql_method method, int64_t m, int64_t n, ql_dtype dtype) {
   (void)m;

@@ -347,6 +347,7 @@ ql_status gram_launch_one(const GramCall& c, const GramWs& w, int pass, int gate
   a.resnorm = c.resnorm;
   a.Rext = c.Rext;
   a.info = c.info;
+  count_launch();
   kern<<<(int)g, Sh::T, Sm::kBytes, c.stream>>>(a);
   return cudaPeekAtLastError() == cudaSuccess ? QL_OK : QL_ERR_CUDA;
 }

@@ -68,5 +68,7 @@ ql_status gram_launch(const GramCall& c, ql_arith arith);
 
 int device_sm_count();
 ql_arith current_arith();
+// Counts every kernel this library launches (reported by ql_launch_count()).
+void count_launch();
 
 }  // namespace ql

@@ -106,6 +106,7 @@ ql_status launch_one(const TsqrCall& c, const TreeView& tv_in, int gated) {
   a.resnorm = c.resnorm;
   a.Rext = c.Rext;
   a.info = c.info;
+  count_launch();
   kern<<<(int)g, T, Sm::kBytes, c.stream>>>(a);
   return cudaPeekAtLastError() == cudaSuccess ? QL_OK : QL_ERR_CUDA;
 }
