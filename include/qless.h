@@ -157,6 +157,14 @@ typedef struct {
 size_t ql_batch_workspace_bytes(int32_t count, const ql_problem* probs);
 ql_status ql_batch_qless(int32_t count, const ql_problem* probs, void* ws, size_t ws_bytes, void* stream);
 
+/* The two halves of ql_batch_qless.  ql_batch_prepare builds the plan on the host, uploads
+ * it into `ws` and waits for the upload (not capturable).  ql_batch_launch clears the
+ * counters and launches the persistent kernel(s) of the plan last prepared in `ws`; it
+ * makes no host synchronisation and allocates nothing, so it can be captured in a CUDA
+ * graph and replayed (the first launch of the process should happen before capture). */
+ql_status ql_batch_prepare(int32_t count, const ql_problem* probs, void* ws, size_t ws_bytes, void* stream);
+ql_status ql_batch_launch(void* ws, void* stream);
+
 /*
  * Autotuner: times the candidate configurations (rows per CTA tile, CTAs per SM, method)
  * for an m x n problem of `dtype` on the current device using scratch inputs in `ws`

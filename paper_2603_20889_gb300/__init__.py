@@ -43,6 +43,8 @@ SIGNATURES = {
     "ql_lstsq_qless": (_i32, [_i64, _i64, _vp, _i64, _vp, _i32, _i32, _dp, _dp, _dp, _vp, _vp, _sz, _vp]),
     "ql_batch_workspace_bytes": (_sz, [_i32, _vp]),
     "ql_batch_qless": (_i32, [_i32, _vp, _vp, _sz, _vp]),
+    "ql_batch_prepare": (_i32, [_i32, _vp, _vp, _sz, _vp]),
+    "ql_batch_launch": (_i32, [_vp, _vp]),
     "ql_autotune_workspace_bytes": (_sz, [_i64, _i64, _i32]),
     "ql_autotune": (_i32, [_i64, _i64, _i32, _f64, _vp, _sz, _vp, _vp, _vp]),
     "ql_autotune_save": (_i32, [ctypes.c_char_p]),
@@ -56,6 +58,32 @@ SIGNATURES = {
     "ql_server_stats": (_i32, [_vp, _vp]),
     "ql_server_destroy": (None, [_vp]),
 }
+
+
+class Problem(ctypes.Structure):
+    """ql_problem: one problem of a batch (device pointers)."""
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("ld", ctypes.c_int64), ("X", ctypes.c_void_p),
+                ("dtype", ctypes.c_int32), ("kind", ctypes.c_int32), ("b", ctypes.c_void_p),
+                ("R", ctypes.c_void_p), ("x", ctypes.c_void_p), ("info", ctypes.c_void_p)]
+
+
+class Request(ctypes.Structure):
+    """ql_request: one serving request (device pointers)."""
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("ld", ctypes.c_int64), ("X", ctypes.c_void_p),
+                ("dtype", ctypes.c_int32), ("kind", ctypes.c_int32), ("b", ctypes.c_void_p),
+                ("kappa_hint", ctypes.c_double)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("index", ctypes.c_int32), ("latency_ms", ctypes.c_double),
+                ("R", ctypes.c_void_p), ("x", ctypes.c_void_p)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("rejected", ctypes.c_int64),
+                ("in_flight", ctypes.c_int64), ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("mean_ms", ctypes.c_double), ("solves_per_s", ctypes.c_double),
+                ("hbm_in_use_bytes", ctypes.c_double), ("hbm_peak_bytes", ctypes.c_double)]
 
 
 class QlError(RuntimeError):
@@ -203,3 +231,59 @@ def lstsq_qless(A, b, method=QL_TSQR, want_rext=False, info=None, ws=None, strea
                                        info.data_ptr(), ws.data_ptr(), ws.numel(), _stream_ptr(stream))
     _check(st, "ql_lstsq_qless")
     return x, rn, Rext, info
+
+
+def batch_qless(problems, ws=None, stream=None, device=None):
+    """Run a list of Problem structs in one batched launch; returns the workspace used."""
+    torch = _torch()
+    arr = (Problem * len(problems))(*problems)
+    lib = load_library()
+    nb = lib.ql_batch_workspace_bytes(len(problems), arr)
+    if nb == 0:
+        raise QlError(QL_ERR_ARG, "ql_batch_workspace_bytes")
+    if ws is None or ws.numel() < nb:
+        ws = torch.empty(nb, dtype=torch.uint8, device=device or "cuda")
+    _check(lib.ql_batch_qless(len(problems), arr, ws.data_ptr(), ws.numel(), _stream_ptr(stream)), "ql_batch_qless")
+    return ws
+
+
+class Server:
+    """Thin owner of a ql_server handle."""
+
+    def __init__(self, hbm_budget_bytes: int, max_slots: int = 4096, streams: int = 4):
+        self.lib = load_library()
+        self.h = self.lib.ql_server_create(hbm_budget_bytes, max_slots, streams)
+        if not self.h:
+            raise QlError(QL_ERR_CUDA, "ql_server_create")
+
+    def submit(self, req: Request) -> int:
+        t = ctypes.c_uint64(0)
+        _check(self.lib.ql_server_submit(self.h, ctypes.byref(req), ctypes.byref(t)), "ql_server_submit")
+        return t.value
+
+    def poll(self, ticket: int):
+        r = Result()
+        st = self.lib.ql_server_poll(self.h, ticket, ctypes.byref(r))
+        return st, r
+
+    def release(self, ticket: int):
+        return self.lib.ql_server_release(self.h, ticket)
+
+    def drain(self, timeout_s: float = 60.0):
+        return self.lib.ql_server_drain(self.h, timeout_s)
+
+    def stats(self) -> Stats:
+        st = Stats()
+        _check(self.lib.ql_server_stats(self.h, ctypes.byref(st)), "ql_server_stats")
+        return st
+
+    def close(self):
+        if self.h:
+            self.lib.ql_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

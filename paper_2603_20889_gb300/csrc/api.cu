@@ -78,6 +78,8 @@ ql_status ql_tsqr_qless(int64_t m, int64_t n, const void* X, ql_dtype dtype, int
   c.ws = ws;
   c.ws_bytes = ws_bytes;
   c.stream = (cudaStream_t)stream;
+  int ctas = 0;
+  if (tune_lookup(m, n, dtype, 1.0, nullptr, &ctas)) c.ctas_per_sm = ctas;
   return tsqr_launch(c, current_arith());
 }
 
@@ -126,7 +128,7 @@ ql_status ql_lstsq_qless(int64_t m, int64_t n, const void* A, int64_t lda, const
   if (st) return st;
   if ((m > 0 && !b) || !x || !resnorm) return QL_ERR_ARG;
   if (b && !elem_aligned(b, dtype)) return QL_ERR_ALIGN;
-  if (method == QL_AUTO) method = QL_TSQR;
+  if (method == QL_AUTO) method = ql_autotune_choose(m, n + 1, dtype, 1.0);
   if (method == QL_TSQR) {
     TsqrCall c;
     c.m = m;

@@ -1,0 +1,204 @@
+// Project autotuner: for an (m, n, dtype, kappa) class it times the candidate
+// configurations on the current GPU -- TSQR with 1 or 2 CTAs per SM (which sets the
+// number of R-tree leaves and the rows per CTA) and Cholesky-QR2 when the condition hint
+// allows it (kappa <= 1e6, where the Gram method stays within the accuracy bound) -- and
+// records the fastest in a process-wide table that ql_autotune_choose() and the QL_AUTO
+// paths consult.  The table persists as a small JSON text file.
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+
+#include "internal.h"
+
+namespace ql {
+
+struct TuneKey {
+  int dtype, n, mlog2, kbucket;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(dtype, n, mlog2, kbucket) < std::tie(o.dtype, o.n, o.mlog2, o.kbucket);
+  }
+};
+struct TuneVal {
+  int method;  // QL_TSQR or QL_CHOLQR2
+  int ctas_per_sm;
+  double ms;
+};
+
+static std::mutex g_tune_mu;
+static std::map<TuneKey, TuneVal> g_tune;
+
+static TuneKey key_of(int64_t m, int64_t n, ql_dtype dt, double kappa) {
+  int ml = 0;
+  while ((1ll << (ml + 1)) <= m && ml < 62) ++ml;
+  return TuneKey{(int)dt, (int)n, ml, kappa > 1e6 ? 1 : 0};
+}
+
+bool tune_lookup(int64_t m, int64_t n, ql_dtype dt, double kappa, int* method, int* ctas) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tune.find(key_of(m, n, dt, kappa));
+  if (it == g_tune.end()) return false;
+  if (method) *method = it->second.method;
+  if (ctas) *ctas = it->second.ctas_per_sm;
+  return true;
+}
+
+// Scratch input: a hash-based pseudo-random matrix in [-1, 1) (a distinct splitmix64
+// value per entry); only its shape matters for timing.
+template <typename S>
+__global__ void fill_kernel(S* x, int64_t count, uint64_t seed) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t z = seed + (uint64_t)i * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    x[i] = (S)((double)(z >> 11) * 0x1p-52 - 1.0);
+  }
+}
+
+}  // namespace ql
+
+using namespace ql;
+
+extern "C" {
+
+size_t ql_autotune_workspace_bytes(int64_t m, int64_t n, ql_dtype dtype) {
+  if (m < 1 || n < 1 || n > 64) return 0;
+  size_t el = dtype == QL_F64 ? 8 : 4;
+  size_t x = ((size_t)m * n * el + 255) / 256 * 256;
+  size_t t = tsqr_workspace_bytes((int)n), g = gram_workspace_bytes((int)n);
+  return x + (t > g ? t : g) + 256 + 8 * 64 * 64;
+}
+
+ql_status ql_autotune(int64_t m, int64_t n, ql_dtype dtype, double kappa_hint, void* ws, size_t ws_bytes,
+                      void* stream, ql_method* method_out, double* ms_out) {
+  size_t need = ql_autotune_workspace_bytes(m, n, dtype);
+  if (need == 0) return QL_ERR_ARG;
+  if (!ws || ws_bytes < need) return QL_ERR_WORKSPACE;
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned char* w = static_cast<unsigned char*>(ws);
+  size_t el = dtype == QL_F64 ? 8 : 4;
+  size_t xb = ((size_t)m * n * el + 255) / 256 * 256;
+  void* X = w;
+  double* R = reinterpret_cast<double*>(w + xb);
+  int32_t* info = reinterpret_cast<int32_t*>(w + xb + 8 * 64 * 64);
+  void* sws = w + xb + 8 * 64 * 64 + 256;
+  size_t swsb = ws_bytes - (xb + 8 * 64 * 64 + 256);
+  if (dtype == QL_F64)
+    fill_kernel<double><<<1024, 256, 0, st>>>(static_cast<double*>(X), m * n, 12345);
+  else
+    fill_kernel<float><<<1024, 256, 0, st>>>(static_cast<float*>(X), m * n, 12345);
+  count_launch();
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  struct Cand {
+    int method, ctas;
+  };
+  Cand cands[3] = {{QL_TSQR, 1}, {QL_TSQR, 2}, {QL_CHOLQR2, 0}};
+  int ncand = kappa_hint > 1e6 ? 2 : 3;
+  TuneVal best{QL_TSQR, 0, 1e30};
+  for (int ci = 0; ci < ncand; ++ci) {
+    auto run = [&]() -> ql_status {
+      if (cands[ci].method == QL_TSQR) {
+        TsqrCall c;
+        c.m = m;
+        c.n = (int)n;
+        c.nA = (int)n;
+        c.A = X;
+        c.lda = m;
+        c.b = X;
+        c.dtype = dtype;
+        c.R = R;
+        c.ldr = n;
+        c.info = info;
+        c.ws = sws;
+        c.ws_bytes = swsb;
+        c.stream = st;
+        c.ctas_per_sm = cands[ci].ctas;
+        return tsqr_launch(c, current_arith());
+      }
+      return ql_cholqr2_qless(m, n, X, dtype, m, R, n, info, sws, swsb, stream);
+    };
+    ql_status s = run();
+    if (s != QL_OK) continue;
+    float best_ms = 1e30f;
+    for (int rep = 0; rep < 3; ++rep) {
+      cudaEventRecord(e0, st);
+      run();
+      cudaEventRecord(e1, st);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best_ms) best_ms = ms;
+    }
+    if (best_ms < best.ms) best = TuneVal{cands[ci].method, cands[ci].ctas, best_ms};
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return QL_ERR_CUDA;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key_of(m, n, dtype, kappa_hint)] = best;
+  }
+  if (method_out) *method_out = best.method;
+  if (ms_out) *ms_out = best.ms;
+  return QL_OK;
+}
+
+ql_method ql_autotune_choose(int64_t m, int64_t n, ql_dtype dtype, double kappa_hint) {
+  int method = QL_TSQR;
+  if (tune_lookup(m, n, dtype, kappa_hint, &method, nullptr)) return method;
+  // model: Householder TSQR reads X once and is stable for every kappa
+  return QL_TSQR;
+}
+
+ql_status ql_autotune_save(const char* path) {
+  if (!path) return QL_ERR_ARG;
+  FILE* f = std::fopen(path, "w");
+  if (!f) return QL_ERR_ARG;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  std::fprintf(f, "{\"arch\": \"sm_103a\", \"entries\": [");
+  bool first = true;
+  for (auto& e : g_tune) {
+    std::fprintf(f, "%s\n {\"dtype\": %d, \"n\": %d, \"mlog2\": %d, \"kbucket\": %d, \"method\": %d, \"ctas\": %d, \"ms\": %.6f}",
+                 first ? "" : ",", e.first.dtype, e.first.n, e.first.mlog2, e.first.kbucket, e.second.method,
+                 e.second.ctas_per_sm, e.second.ms);
+    first = false;
+  }
+  std::fprintf(f, "\n]}\n");
+  std::fclose(f);
+  return QL_OK;
+}
+
+ql_status ql_autotune_load(const char* path) {
+  if (!path) return QL_ERR_ARG;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return QL_ERR_ARG;
+  std::string s;
+  char buf[4096];
+  size_t k;
+  while ((k = std::fread(buf, 1, sizeof(buf), f)) > 0) s.append(buf, k);
+  std::fclose(f);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  size_t pos = 0;
+  int loaded = 0;
+  while ((pos = s.find("{\"dtype\"", pos)) != std::string::npos) {
+    TuneKey key{};
+    TuneVal val{};
+    if (std::sscanf(s.c_str() + pos,
+                    "{\"dtype\": %d, \"n\": %d, \"mlog2\": %d, \"kbucket\": %d, \"method\": %d, \"ctas\": %d, \"ms\": %lf}",
+                    &key.dtype, &key.n, &key.mlog2, &key.kbucket, &val.method, &val.ctas_per_sm, &val.ms) == 7) {
+      g_tune[key] = val;
+      ++loaded;
+    }
+    pos += 8;
+  }
+  return loaded > 0 || s.find("\"entries\"") != std::string::npos ? QL_OK : QL_ERR_ARG;
+}
+
+}  // extern "C"

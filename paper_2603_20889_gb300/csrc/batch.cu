@@ -1,0 +1,389 @@
+// Batched Q-less TSQR: many uneven problems in ONE persistent launch.
+//
+// The host plan splits every problem into chunks of row tiles (the leaves of that
+// problem's R-tree) and orders the problems by decreasing work.  A fixed grid of
+// persistent CTAs claims chunks through one atomic counter; a CTA factors its chunk with
+// the single-problem tile machinery (tsqr.cuh) of the problem's column class, stores the
+// leaf triangle and climbs that problem's tree; whoever completes a root writes R (or the
+// least-squares solution).  Problems whose data leave the double-float range are redone
+// by a second, gated FP64 launch that only touches flagged problems.
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "epilogue.cuh"
+#include "internal.h"
+#include "tsqr.cuh"
+
+namespace ql {
+
+// Column classes of the batched kernel: NC, TC, RPT at T = 128 threads.
+template <int NC> struct BatchCls;
+template <> struct BatchCls<4> { static constexpr int TC = 1, RPT = 16; };
+template <> struct BatchCls<8> { static constexpr int TC = 1, RPT = 8; };
+template <> struct BatchCls<16> { static constexpr int TC = 2, RPT = 8; };
+template <> struct BatchCls<32> { static constexpr int TC = 4, RPT = 8; };
+template <> struct BatchCls<64> { static constexpr int TC = 8, RPT = 8; };
+constexpr int kBatchT = 128;
+
+static int class_of(int n) { return n <= 4 ? 4 : n <= 8 ? 8 : n <= 16 ? 16 : n <= 32 ? 32 : 64; }
+template <int NC>
+__host__ __device__ constexpr int rows_per_tile() {
+  return (kBatchT / BatchCls<NC>::TC) * BatchCls<NC>::RPT;
+}
+static int rows_per_tile_rt(int nc) {
+  switch (nc) {
+    case 4: return rows_per_tile<4>();
+    case 8: return rows_per_tile<8>();
+    case 16: return rows_per_tile<16>();
+    case 32: return rows_per_tile<32>();
+    default: return rows_per_tile<64>();
+  }
+}
+
+// Per-problem plan entry (device copy lives in the workspace).
+struct BatchItem {
+  const void* A;
+  const void* b;
+  int64_t m, lda;
+  int n;       // columns factored (n + 1 for least squares)
+  int nA;      // columns from A
+  int nc;      // column class
+  int dtype;
+  int kind;    // 0 R, 1 lstsq
+  int chunks;  // leaves
+  int64_t tiles, tiles_per_chunk;
+  int64_t work_begin;  // prefix of chunks over the ordered problems
+  int64_t slot_off;    // in doubles
+  int64_t cnt_off;     // in ints
+  double* R;
+  double* x;
+  int32_t* info;
+  int flag_idx;
+};
+
+struct BatchHeader {
+  int work_counter[2];  // [0] double-float launch, [1] gated FP64 launch
+  int count;
+  int pad;
+  int64_t total_work;
+};
+
+template <int NC, typename S, typename Ar>
+QL_DEV void batch_chunk(const BatchItem& it, int64_t chunk, unsigned char* smem, double* slots, int* counters,
+                        int* flags) {
+  constexpr int TC = BatchCls<NC>::TC, RPT = BatchCls<NC>::RPT, T = kBatchT;
+  using Cta = TsqrCta<NC, TC, RPT, T, S, Ar>;
+  Cta cta;
+  cta.init(smem);
+  cta.reset_r();
+  if (threadIdx.x == 0) cta.misc[0] = 0;
+  __syncthreads();
+  TsqrProblem<S> p;
+  p.src.A = static_cast<const S*>(it.A);
+  p.src.lda = it.lda;
+  p.src.b = static_cast<const S*>(it.b);
+  p.src.nA = it.nA;
+  p.m = it.m;
+  p.n = it.n;
+  const int64_t t0 = chunk * it.tiles_per_chunk;
+  const int64_t t1 = min(it.tiles, t0 + it.tiles_per_chunk);
+  cta.run(p, 0, t0, t1);
+  const int n = it.n;
+  if (threadIdx.x == 0 && cta.out_of_range(n)) {
+    atomicOr(&flags[it.flag_idx], 1);
+    atomicOr(&flags[-1], 1);  // any_flag lives just before the per-problem flags
+  }
+  TreeView tv;
+  tv.slots = slots + it.slot_off;
+  tv.counters = counters + it.cnt_off;
+  tv.flags = flags + it.flag_idx;
+  tv.leaves = it.chunks;
+  double* slot = tv.slots + (size_t)chunk * n * n;
+  for (int i = threadIdx.x; i < n * n; i += T) {
+    int c = i / n, r = i % n;
+    __stcg(slot + i, r <= c ? Ar::to_double(cta.R[r * NC + c]) : 0.0);
+  }
+  double* Ra = cta.arena;
+  double* Rb = cta.arena + NC * NC;
+  if (!climb_tree<NC, T>(tv, (int)chunk, n, Ra, Rb, cta.sd, &cta.misc[1])) return;
+  __threadfence();
+  if (Ar::kRangeChecked && *(volatile int*)&flags[it.flag_idx] != 0) return;
+  if (it.kind == 0)
+    epilogue_r<T>(Ra, NC, n, it.R, n, it.info, &cta.misc[2]);
+  else
+    epilogue_lstsq<T>(Ra, NC, n, it.x, it.x + (n - 1), it.R, it.info, cta.sd, &cta.misc[2]);
+  __syncthreads();
+}
+
+template <typename S, typename Ar>
+QL_DEV void batch_dispatch(const BatchItem& it, int64_t chunk, unsigned char* smem, double* slots, int* counters,
+                           int* flags) {
+  switch (it.nc) {
+    case 4: batch_chunk<4, S, Ar>(it, chunk, smem, slots, counters, flags); break;
+    case 8: batch_chunk<8, S, Ar>(it, chunk, smem, slots, counters, flags); break;
+    case 16: batch_chunk<16, S, Ar>(it, chunk, smem, slots, counters, flags); break;
+    case 32: batch_chunk<32, S, Ar>(it, chunk, smem, slots, counters, flags); break;
+    default: batch_chunk<64, S, Ar>(it, chunk, smem, slots, counters, flags); break;
+  }
+}
+
+template <typename Ar>
+__global__ void __launch_bounds__(kBatchT, 1)
+    batch_kernel(BatchHeader* hdr, const BatchItem* items, int count, double* slots, int* counters, int* flags,
+                 int gated) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int64_t s_work;
+  __shared__ int s_item;
+  if (gated && *(volatile int*)&flags[-1] == 0) return;  // no problem left the range
+  const int64_t total = hdr->total_work;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      s_work = atomicAdd(&hdr->work_counter[gated ? 1 : 0], 1);
+      // last problem whose work_begin <= s_work (items ordered by work_begin)
+      int lo = 0, hi = count - 1;
+      while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (items[mid].work_begin <= s_work) lo = mid;
+        else hi = mid - 1;
+      }
+      s_item = lo;
+    }
+    __syncthreads();
+    const int64_t w = s_work;
+    const int idx = s_item;
+    __syncthreads();
+    if (w >= total) break;
+    const BatchItem it = items[idx];
+    if (gated && *(volatile int*)&flags[it.flag_idx] == 0) continue;
+    const int64_t chunk = w - it.work_begin;
+    if (it.dtype == QL_F64)
+      batch_dispatch<double, Ar>(it, chunk, smem, slots, counters, flags);
+    else
+      batch_dispatch<float, Ar>(it, chunk, smem, slots, counters, flags);
+    __syncthreads();
+  }
+}
+
+template <typename Ar>
+static size_t batch_smem_bytes() {
+  size_t b = 0;
+  b = std::max(b, TsqrSmem<4, 1, 16, kBatchT, float, Ar>::kBytes);
+  b = std::max(b, TsqrSmem<64, 8, 8, kBatchT, float, Ar>::kBytes);
+  b = std::max(b, TsqrSmem<4, 1, 16, kBatchT, double, Ar>::kBytes);
+  b = std::max(b, TsqrSmem<8, 1, 8, kBatchT, double, Ar>::kBytes);
+  b = std::max(b, TsqrSmem<16, 2, 8, kBatchT, double, Ar>::kBytes);
+  b = std::max(b, TsqrSmem<32, 4, 8, kBatchT, double, Ar>::kBytes);
+  b = std::max(b, TsqrSmem<64, 8, 8, kBatchT, double, Ar>::kBytes);
+  return b;
+}
+
+// ---------------------------------------------------------------------------------------
+// Host plan
+// ---------------------------------------------------------------------------------------
+
+struct BatchPlan {
+  std::vector<BatchItem> items;
+  size_t off_items = 0, off_flags = 0, off_counters = 0, off_slots = 0, bytes = 0;
+  int64_t total_work = 0;
+};
+
+// Tiles per chunk: aim for chunks of about kTargetRows rows (fewer, longer chunks for
+// wide problems keep their FP64 tree merges cheap), overridable by the tuner.
+static int64_t g_target_rows = 1 << 15;
+
+static bool make_plan(int32_t count, const ql_problem* probs, BatchPlan& P) {
+  P.items.clear();
+  std::vector<int> order(count);
+  for (int i = 0; i < count; ++i) order[i] = i;
+  auto work = [&](int i) { return (double)probs[i].m * probs[i].n * probs[i].n; };
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work(a) > work(b); });
+  int64_t slots = 0, cnts = 0, wb = 0;
+  for (int k = 0; k < count; ++k) {
+    const ql_problem& pr = probs[order[k]];
+    if (pr.m < 0 || pr.n < 1 || pr.n > 64 || (pr.kind == 1 && pr.n > 63)) return false;
+    if (pr.ld < (pr.m > 1 ? pr.m : 1) || (pr.dtype != QL_F64 && pr.dtype != QL_F32)) return false;
+    if (!pr.R || (pr.kind == 1 && (!pr.x || !pr.b)) || (pr.m > 0 && !pr.X)) return false;
+    BatchItem it{};
+    it.A = pr.X;
+    it.b = pr.kind == 1 ? pr.b : pr.X;
+    it.m = pr.m;
+    it.lda = pr.ld;
+    it.nA = (int)pr.n;
+    it.n = (int)pr.n + (pr.kind == 1 ? 1 : 0);
+    it.nc = class_of(it.n);
+    it.dtype = pr.dtype;
+    it.kind = pr.kind;
+    const int B = rows_per_tile_rt(it.nc);
+    it.tiles = (pr.m + B - 1) / B;
+    int64_t tpc = std::max<int64_t>(1, g_target_rows / B);
+    it.chunks = (int)std::max<int64_t>(1, (it.tiles + tpc - 1) / tpc);
+    if (it.chunks > 4096) {  // keep trees shallow
+      it.chunks = 4096;
+      tpc = (it.tiles + 4095) / 4096;
+    }
+    it.tiles_per_chunk = tpc;
+    it.work_begin = wb;
+    wb += it.chunks;
+    it.slot_off = slots;
+    slots += (int64_t)tree_slots(it.chunks) * it.n * it.n;
+    it.cnt_off = cnts;
+    cnts += (int64_t)tree_counters(it.chunks);
+    it.R = pr.R;
+    it.x = pr.x;
+    it.info = pr.info;
+    it.flag_idx = k;
+    P.items.push_back(it);
+  }
+  P.total_work = wb;
+  size_t off = (sizeof(BatchHeader) + 255) / 256 * 256;
+  P.off_items = off;
+  off += (count * sizeof(BatchItem) + 255) / 256 * 256;
+  P.off_flags = off;  // any_flag at [0], per-problem flags from [1]
+  off += ((count + 1) * sizeof(int) + 255) / 256 * 256;
+  P.off_counters = off;
+  off += (cnts * sizeof(int) + 255) / 256 * 256;
+  P.off_slots = off;
+  off += slots * sizeof(double);
+  P.bytes = off;
+  return true;
+}
+
+template <typename Ar>
+static ql_status launch_batch(unsigned char* ws, const BatchPlan& P, int count, cudaStream_t stream, int gated) {
+  static int occ = 0;
+  static size_t smem = 0;
+  static std::mutex mu;
+  auto kern = batch_kernel<Ar>;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (occ == 0) {
+      smem = batch_smem_bytes<Ar>();
+      if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return QL_ERR_CUDA;
+      int o = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, kBatchT, smem) != cudaSuccess) return QL_ERR_CUDA;
+      occ = o < 1 ? 1 : o;
+    }
+  }
+  int grid = device_sm_count() * occ;
+  if (P.total_work < grid) grid = (int)std::max<int64_t>(1, P.total_work);
+  count_launch();
+  kern<<<grid, kBatchT, smem, stream>>>(reinterpret_cast<BatchHeader*>(ws),
+                                         reinterpret_cast<const BatchItem*>(ws + P.off_items), count,
+                                         reinterpret_cast<double*>(ws + P.off_slots),
+                                         reinterpret_cast<int*>(ws + P.off_counters),
+                                         reinterpret_cast<int*>(ws + P.off_flags) + 1, gated);
+  return cudaPeekAtLastError() == cudaSuccess ? QL_OK : QL_ERR_CUDA;
+}
+
+// The plan of the last ql_batch_prepare per workspace pointer (for ql_batch_launch).
+struct PlanCache {
+  std::mutex mu;
+  std::vector<std::pair<void*, BatchPlan>> plans;
+  void put(void* ws, const BatchPlan& p) {
+    std::lock_guard<std::mutex> lk(mu);
+    for (auto& e : plans)
+      if (e.first == ws) {
+        e.second = p;
+        return;
+      }
+    plans.emplace_back(ws, p);
+  }
+  bool get(void* ws, BatchPlan& p) {
+    std::lock_guard<std::mutex> lk(mu);
+    for (auto& e : plans)
+      if (e.first == ws) {
+        p = e.second;
+        return true;
+      }
+    return false;
+  }
+};
+static PlanCache g_plans;
+
+void set_batch_target_rows(int64_t rows) { g_target_rows = rows < 256 ? 256 : rows; }
+int64_t batch_target_rows() { return g_target_rows; }
+
+// Asynchronous plan upload through a caller-owned pinned staging buffer (the serving
+// loop's path: no host synchronisation).  The staging bytes must stay untouched until the
+// stream has passed the copy.
+ql_status batch_prepare_async(int32_t count, const ql_problem* probs, void* ws, size_t ws_bytes, cudaStream_t st,
+                              unsigned char* pinned, size_t pinned_bytes) {
+  if (count < 1 || !probs) return QL_ERR_ARG;
+  BatchPlan P;
+  if (!make_plan(count, probs, P)) return QL_ERR_ARG;
+  if (!ws || ws_bytes < P.bytes) return QL_ERR_WORKSPACE;
+  if (!pinned || pinned_bytes < P.off_flags) return QL_ERR_WORKSPACE;
+  BatchHeader h{};
+  h.count = count;
+  h.total_work = P.total_work;
+  std::memcpy(pinned, &h, sizeof(h));
+  std::memcpy(pinned + P.off_items, P.items.data(), P.items.size() * sizeof(BatchItem));
+  if (cudaMemcpyAsync(ws, pinned, P.off_flags, cudaMemcpyHostToDevice, st) != cudaSuccess) return QL_ERR_CUDA;
+  g_plans.put(ws, P);
+  return QL_OK;
+}
+
+size_t batch_plan_upload_bytes(int32_t count, const ql_problem* probs) {
+  BatchPlan P;
+  if (count < 1 || !probs || !make_plan(count, probs, P)) return 0;
+  return P.off_flags;
+}
+
+}  // namespace ql
+
+using namespace ql;
+
+extern "C" {
+
+size_t ql_batch_workspace_bytes(int32_t count, const ql_problem* probs) {
+  if (count < 1 || !probs) return 0;
+  BatchPlan P;
+  if (!make_plan(count, probs, P)) return 0;
+  return P.bytes;
+}
+
+ql_status ql_batch_prepare(int32_t count, const ql_problem* probs, void* ws, size_t ws_bytes, void* stream) {
+  if (count < 1 || !probs) return QL_ERR_ARG;
+  BatchPlan P;
+  if (!make_plan(count, probs, P)) return QL_ERR_ARG;
+  if (!ws || ws_bytes < P.bytes) return QL_ERR_WORKSPACE;
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned char* w = static_cast<unsigned char*>(ws);
+  BatchHeader h{};
+  h.count = count;
+  h.total_work = P.total_work;
+  // pageable host sources: cudaMemcpyAsync returns once the data is staged
+  if (cudaMemcpyAsync(w, &h, sizeof(h), cudaMemcpyHostToDevice, st) != cudaSuccess) return QL_ERR_CUDA;
+  if (cudaMemcpyAsync(w + P.off_items, P.items.data(), P.items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice,
+                      st) != cudaSuccess)
+    return QL_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return QL_ERR_CUDA;
+  g_plans.put(ws, P);
+  return QL_OK;
+}
+
+ql_status ql_batch_launch(void* ws, void* stream) {
+  BatchPlan P;
+  if (!ws || !g_plans.get(ws, P)) return QL_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned char* w = static_cast<unsigned char*>(ws);
+  const int count = (int)P.items.size();
+  // counters, flags and the work counters start at zero on every launch
+  if (cudaMemsetAsync(w, 0, 2 * sizeof(int), st) != cudaSuccess) return QL_ERR_CUDA;
+  if (cudaMemsetAsync(w + P.off_flags, 0, P.off_slots - P.off_flags, st) != cudaSuccess) return QL_ERR_CUDA;
+  ql_status s = current_arith() == QL_ARITH_F64 ? launch_batch<ArithF64>(w, P, count, st, 0)
+                                                : launch_batch<ArithDF>(w, P, count, st, 0);
+  if (s != QL_OK || current_arith() == QL_ARITH_F64) return s;
+  return launch_batch<ArithF64>(w, P, count, st, 1);
+}
+
+ql_status ql_batch_qless(int32_t count, const ql_problem* probs, void* ws, size_t ws_bytes, void* stream) {
+  ql_status s = ql_batch_prepare(count, probs, ws, ws_bytes, stream);
+  if (s != QL_OK) return s;
+  return ql_batch_launch(ws, stream);
+}
+
+}  // extern "C"

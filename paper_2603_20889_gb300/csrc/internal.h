@@ -71,4 +71,12 @@ ql_arith current_arith();
 // Counts every kernel this library launches (reported by ql_launch_count()).
 void count_launch();
 
+// Autotune table lookup (method, CTAs per SM) for an (m, n, dtype, kappa) class.
+bool tune_lookup(int64_t m, int64_t n, ql_dtype dt, double kappa, int* method, int* ctas);
+
+// Batched path, asynchronous plan upload through pinned staging (serving loop).
+ql_status batch_prepare_async(int32_t count, const ql_problem* probs, void* ws, size_t ws_bytes, cudaStream_t st,
+                              unsigned char* pinned, size_t pinned_bytes);
+size_t batch_plan_upload_bytes(int32_t count, const ql_problem* probs);
+
 }  // namespace ql
