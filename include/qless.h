@@ -99,6 +99,23 @@ ql_status ql_tsqr_qless(int64_t m, int64_t n, const void* X, ql_dtype dtype, int
                         int64_t ldr, int32_t* info, void* ws, size_t ws_bytes, void* stream);
 
 /*
+ * TSQR for callers that cannot allocate device memory (the paper has no counterpart: it is
+ * an interface addition of this library).  Same computation and arguments as
+ * ql_tsqr_qless, without the workspace: code running while its stream is captured into a
+ * CUDA graph may not call cudaMalloc, host callbacks must not, and extensions of
+ * frameworks that route every device allocation through their own pools often have no
+ * allocator to call.  The scratch lives in a fixed 4 MiB array inside the library that
+ * every GPU loading the library keeps until the process exits; n <= 16 is supported (any
+ * m), larger n returns QL_ERR_WORKSPACE.  No cudaMalloc, cudaFree or other allocating
+ * call is made.  The first call on a device looks up the array's device address (with that
+ * device current) and should come before any stream capture.  All calls share the one
+ * array: calls that overlap on the GPU (different streams, or different host threads)
+ * race and must be serialised by the caller.
+ */
+ql_status ql_tsqr_qless_noalloc(int64_t m, int64_t n, const void* X, ql_dtype dtype, int64_t ldx, double* R,
+                                int64_t ldr, int32_t* info, void* stream);
+
+/*
  * Q-less Cholesky-QR2 (Sec. 3.1, Algorithm 1): C = X^T X; R1 = chol(C); C = (X R1^{-1})^T
  * (X R1^{-1}) with X R1^{-1} formed tile by tile and never stored; R2 = chol(C); R = R2 R1.
  * Both Cholesky factorisations, R1^{-1} and R2 R1 run on the device in FP64.  A

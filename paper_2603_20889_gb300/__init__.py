@@ -38,6 +38,7 @@ SIGNATURES = {
     "ql_launch_count": (ctypes.c_uint64, []),
     "ql_workspace_bytes": (_sz, [_i32, _i64, _i64, _i32]),
     "ql_tsqr_qless": (_i32, [_i64, _i64, _vp, _i32, _i64, _dp, _i64, _vp, _vp, _sz, _vp]),
+    "ql_tsqr_qless_noalloc": (_i32, [_i64, _i64, _vp, _i32, _i64, _dp, _i64, _vp, _vp]),
     "ql_cholqr2_qless": (_i32, [_i64, _i64, _vp, _i32, _i64, _dp, _i64, _vp, _vp, _sz, _vp]),
     "ql_svqb_qless": (_i32, [_i64, _i64, _vp, _i32, _i64, _dp, _i64, _dp, _f64, _vp, _vp, _sz, _vp]),
     "ql_lstsq_qless": (_i32, [_i64, _i64, _vp, _i64, _vp, _i32, _i32, _dp, _dp, _dp, _vp, _vp, _sz, _vp]),
