@@ -3,7 +3,17 @@
 // pair, two gated FP64 launches follow that run only if the range check fired.
 #include "gram_launch.cuh"
 
+#include <cstdlib>
+
 namespace ql {
+
+bool tc_gram_enabled() {
+  static const bool on = [] {
+    const char* v = std::getenv("QL_GRAM_SIMT");
+    return !(v && v[0] == '1');
+  }();
+  return on;
+}
 
 static int nc_of(int n) { return n <= 1 ? 1 : n <= 2 ? 2 : n <= 4 ? 4 : n <= 8 ? 8 : n <= 16 ? 16 : n <= 32 ? 32 : 64; }
 

@@ -1,0 +1,112 @@
+// Tensor-core Gram pass (bf16 mma.sync) with exact digit slicing.
+//
+// The Gram products C = Y^T Y of the Gram methods (paper Sec. 3.1, "tsmttsm" and the
+// fused second-pass kernels) are dense contractions over the m rows, so they run on the
+// tensor cores.  FP64-level accuracy comes from splitting every value exactly into bf16
+// digits:  for each row tile and column c, e_c is the smallest power of two above the
+// column's largest |y|;  |y| 2^(49 - e_c) is truncated to a 49-bit integer N and written
+// as seven base-128 digits d_1..d_7 (|d_k| <= 127, the sign of y), so
+//   y ~= sum_k d_k 2^(e_c - 7k)      (truncation below 2^(e_c - 49)).
+// Every digit is an integer that bf16 holds exactly, every product d_p d_q < 2^14 is exact,
+// and the tensor cores sum at most 7 digit pairs over at most 128 rows per accumulator,
+// which stays below 2^24: every FP32 accumulator is an exact integer.  Products with the
+// same weight d = p + q (p + q <= 8, the terms above 2^-56 of the leading one) share one
+// accumulator; each is scaled by 2^(e_i + e_j - 7d) (exact) and added into a double-float
+// accumulator per C entry.  The second pass forms Y = X M (M = R1^{-1} or B1) tile by tile
+// in double-float on the FP32 pipes, then slices Y the same way.
+//
+// Warp layout (8 warps): the C tiles (16-row blocks x 8-column blocks) are grouped by row
+// block into units of up to 2 column blocks, and the row tile is split into KS parts, so
+// that every warp owns the same number of units.  Per 16-row k-step a unit loads the A
+// fragments of all 7 digits and the B fragments of all 7 digits once and issues the 28
+// digit-pair MMAs from registers (one shared-memory fragment load feeds up to 7 MMAs).
+#pragma once
+
+#include "common.cuh"
+
+namespace ql {
+
+template <int NC>
+struct TcShape {
+  static constexpr int T = 256;
+  static constexpr int KT = 8192 / NC;                // rows per shared-memory tile
+  static constexpr int LDR = KT + 8;                  // padded digit row (conflict-free ldmatrix)
+  static constexpr int ND = 7;                        // digits per value
+  static constexpr int MR = NC < 16 ? 1 : NC / 16;    // 16-row blocks of C
+  static constexpr int NCB = NC / 8;                  // 8-column blocks of C
+  static constexpr int TILES = MR * NCB;
+  static constexpr int G = NCB < 2 ? NCB : 2;         // column blocks per warp unit
+  static constexpr int GROUPS = TILES / G;
+  static constexpr int KS = GROUPS >= 8 ? 1 : 8 / GROUPS;  // row parts
+  static constexpr int UNITS = GROUPS * KS;
+  static constexpr int U = UNITS / 8;                 // units per warp
+  static constexpr int KPART = KT / KS;               // rows per unit and tile
+  static_assert(UNITS % 8 == 0, "8 warps");
+  static_assert(KPART <= 128 && KPART % 16 == 0, "exact FP32 digit sums");
+};
+
+template <int NC, typename S>
+struct TcSmem {
+  using Sh = TcShape<NC>;
+  static constexpr size_t kStage = sizeof(S) * NC * Sh::KT;
+  static constexpr size_t kStageDf = 8 * (size_t)NC * Sh::KT;  // in-place double-float view
+  static constexpr size_t kStageMax = kStage > kStageDf ? kStage : kStageDf;
+  static constexpr size_t kSlices = 2 * (size_t)Sh::ND * NC * Sh::LDR;
+  static constexpr size_t kOffSlices = (kStageMax + 127) / 128 * 128;
+  static constexpr size_t kOffM = kOffSlices + kSlices;
+  static constexpr size_t kOffPow = kOffM + 8 * (size_t)NC * NC;   // float 2^e_c per column
+  static constexpr size_t kOffExpo = kOffPow + 4 * NC;             // int max exponent per column
+  static constexpr size_t kOffColmax = kOffExpo + 4 * NC;          // int, range check
+  static constexpr size_t kOffZero = (kOffColmax + 4 * NC + 15) / 16 * 16;
+  static constexpr size_t kOffMisc = kOffZero + 16;
+  static constexpr size_t kMain = kOffMisc + 64 * 4;
+  static constexpr size_t kEpi = 8 * (4 * (size_t)NC * NC + 8 * NC) + 64 * 4 + 16;
+  static constexpr size_t kBytes = kMain > kEpi ? kMain : kEpi;
+};
+
+QL_DEV void ldsm_x4(unsigned& r0, unsigned& r1, unsigned& r2, unsigned& r3, const void* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(smem_addr(p)));
+}
+QL_DEV void ldsm_x2(unsigned& r0, unsigned& r1, const void* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n" : "=r"(r0), "=r"(r1) : "r"(smem_addr(p)));
+}
+QL_DEV void mma_bf16(float (&c)[4], unsigned a0, unsigned a1, unsigned a2, unsigned a3, unsigned b0, unsigned b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// bf16 bit pattern of a signed digit (|v| <= 127 converts exactly).
+QL_DEV unsigned bf16_digit(unsigned v, unsigned sign) {
+  return (__float_as_uint(__uint2float_rn(v)) >> 16) | (sign >> 16);
+}
+
+// 49-bit fixed-point magnitude of a double relative to the column's max biased exponent
+// Emax: N = floor(|x| 2^(49 - e)), e = Emax - 1022 (|x| < 2^e).
+QL_DEV unsigned long long fixed_of_double(double x, int Emax, unsigned& sign) {
+  unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  sign = (unsigned)(bits >> 32) & 0x80000000u;
+  int E = (int)((bits >> 52) & 0x7ff);
+  if (E == 0) return 0ull;
+  unsigned long long sig = (bits & 0xfffffffffffffull) | (1ull << 52);
+  int sh = 4 + Emax - E;
+  return sh >= 53 ? 0ull : (sig >> sh);
+}
+
+// Same for a float part of a double-float value (exponents on the float scale): returns
+// floor(|f| 2^(49 - e)) with e = Efmax - 126.
+QL_DEV unsigned long long fixed_of_float(float f, int Efmax) {
+  unsigned b = __float_as_uint(f);
+  int Ef = (int)((b >> 23) & 0xff);
+  if (Ef == 0) return 0ull;
+  unsigned long long sig = (unsigned long long)((b & 0x7fffffu) | 0x800000u);
+  int sh = Ef - Efmax + 25;  // left shift
+  if (sh >= 0) return sig << sh;
+  return -sh >= 24 ? 0ull : (sig >> -sh);
+}
+
+}  // namespace ql

@@ -68,6 +68,10 @@ ql_status gram_launch(const GramCall& c, ql_arith arith);
 
 int device_sm_count();
 ql_arith current_arith();
+// Whether the Gram passes use the tensor-core kernels (double-float mode, n >= 5);
+// the environment variable QL_GRAM_SIMT=1 selects the SIMT kernels instead.
+bool tc_gram_enabled();
+
 // Counts every kernel this library launches (reported by ql_launch_count()).
 void count_launch();
 
