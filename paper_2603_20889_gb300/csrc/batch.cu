@@ -199,6 +199,12 @@ static bool make_plan(int32_t count, const ql_problem* probs, BatchPlan& P) {
   for (int i = 0; i < count; ++i) order[i] = i;
   auto work = [&](int i) { return (double)probs[i].m * probs[i].n * probs[i].n; };
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work(a) > work(b); });
+  // chunk height: the batch's rows split into at least ~4 chunks per persistent CTA
+  // (so a small batch still fills the GPU), between 2048 rows and g_target_rows
+  int64_t total_rows = 0;
+  for (int i = 0; i < count; ++i) total_rows += probs[i].m > 0 ? probs[i].m : 0;
+  const int64_t ctas = (int64_t)device_sm_count() * 2;
+  const int64_t target = std::max<int64_t>(2048, std::min<int64_t>(g_target_rows, total_rows / (4 * ctas)));
   int64_t slots = 0, cnts = 0, wb = 0;
   for (int k = 0; k < count; ++k) {
     const ql_problem& pr = probs[order[k]];
@@ -217,7 +223,7 @@ static bool make_plan(int32_t count, const ql_problem* probs, BatchPlan& P) {
     it.kind = pr.kind;
     const int B = rows_per_tile_rt(it.nc);
     it.tiles = (pr.m + B - 1) / B;
-    int64_t tpc = std::max<int64_t>(1, g_target_rows / B);
+    int64_t tpc = std::max<int64_t>(1, target / B);
     it.chunks = (int)std::max<int64_t>(1, (it.tiles + tpc - 1) / tpc);
     if (it.chunks > 4096) {  // keep trees shallow
       it.chunks = 4096;

@@ -72,6 +72,9 @@ ql_arith current_arith();
 // the environment variable QL_GRAM_SIMT=1 selects the SIMT kernels instead.
 bool tc_gram_enabled();
 
+// Thread-layout variant of the TSQR kernels (environment QL_TSQR_CFG, 0 = default).
+int tsqr_variant();
+
 // Counts every kernel this library launches (reported by ql_launch_count()).
 void count_launch();
 

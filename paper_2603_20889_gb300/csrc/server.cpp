@@ -3,13 +3,17 @@
 // Requests reference device-resident matrices owned by the caller.  A scheduler thread
 // admits queued requests (FIFO) while the in-flight request count stays within max_slots
 // and the HBM budget covers the request's data plus the server's own device buffers
-// (outputs and batch workspace, carved from one arena allocated at creation), launches
-// every admitted group as ONE batched persistent kernel (ql_batch_launch) on the next of
-// its CUDA streams -- so groups that arrive while others run overlap on the device -- and
-// completes groups when their events fire.  Plans are uploaded through a pinned staging
-// ring, so the scheduler never blocks on the device.  Latency is measured from submit to
-// the scheduler observing the group's completion event.
+// (outputs and batch workspace, carved from one arena allocated at creation), and launches
+// every admitted group as ONE batched persistent kernel (ql_batch_launch) on an idle one
+// of its CUDA streams: each stream runs one group at a time, so requests that arrive while
+// groups run coalesce into the next group, and the groups of different streams overlap on
+// the device.  Groups complete when their events fire; one device-to-host copy per group
+// returns all statuses.  Plans are uploaded through a pinned staging ring, so the
+// scheduler never blocks on the device.  Latency is measured from submit to the scheduler
+// observing the group's completion event.
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -89,9 +93,20 @@ struct Req {
 struct Group {
   std::vector<uint64_t> tickets;
   cudaEvent_t ev = nullptr;
+  int stream = 0;
   size_t ws_off = 0, ws_bytes = 0, pin_off = 0, pin_bytes = 0;
   size_t data_bytes = 0;
+  double t_launch = 0;
 };
+
+// QL_SERVER_TRACE=1 prints one line per completed group (size, launch -> completion time).
+static bool trace_on() {
+  static const bool on = [] {
+    const char* v = std::getenv("QL_SERVER_TRACE");
+    return v && v[0] == '1';
+  }();
+  return on;
+}
 
 }  // namespace ql
 
@@ -100,7 +115,7 @@ struct ql_server {
   size_t budget = 0;
   int max_slots = 0;
   std::vector<cudaStream_t> streams;
-  int next_stream = 0;
+  std::vector<int> stream_busy;  // one group in flight per stream
   unsigned char* dev_base = nullptr;
   ql::Arena dev;
   unsigned char* pin_base = nullptr;
@@ -137,6 +152,9 @@ static void complete_groups(ql_server* s) {
       continue;
     }
     double t = now_s();
+    if (trace_on())
+      std::fprintf(stderr, "[ql_server] group of %zu on stream %d: %.3f ms, %.1f MB data\n", G.tickets.size(),
+                   G.stream, (t - G.t_launch) * 1e3, G.data_bytes / 1e6);
     for (uint64_t tk : G.tickets) {
       Req& q = s->reqs[tk];
       q.state = 2;
@@ -151,6 +169,7 @@ static void complete_groups(ql_server* s) {
     s->dev.release(G.ws_off, G.ws_bytes);
     s->pin.release(G.pin_off, G.pin_bytes);
     s->data_in_flight -= G.data_bytes;
+    s->stream_busy[G.stream] = 0;
     cudaEventDestroy(G.ev);
     s->inflight.erase(s->inflight.begin() + g);
   }
@@ -159,6 +178,15 @@ static void complete_groups(ql_server* s) {
 // Admit queued requests into one group and launch it; returns whether a group started.
 static bool admit_and_launch(ql_server* s) {
   if (s->queue.empty()) return false;
+  // a group starts only on an idle stream: requests that arrive meanwhile coalesce into the
+  // next, larger group (continuous batching across the streams)
+  int sidx = -1;
+  for (int i = 0; i < (int)s->streams.size(); ++i)
+    if (!s->stream_busy[i]) {
+      sidx = i;
+      break;
+    }
+  if (sidx < 0) return false;
   std::vector<uint64_t> group;
   size_t data = 0;
   while (!s->queue.empty() && s->inflight_reqs + (int64_t)group.size() < s->max_slots) {
@@ -188,45 +216,51 @@ static bool admit_and_launch(ql_server* s) {
     p.b = q.r.b;
     p.R = base;
     p.x = base + n1 * n1;
-    p.info = reinterpret_cast<int32_t*>(base + n1 * n1 + n1 + 1);
+    p.info = nullptr;  // set below: one status array per group
   }
-  size_t wsb = ql_batch_workspace_bytes((int32_t)probs.size(), probs.data());
-  size_t upb = batch_plan_upload_bytes((int32_t)probs.size(), probs.data());
-  size_t infob = probs.size() * 2 * sizeof(int32_t);
+  // The group's workspace (R-trees) must fit next to its data and outputs: drop requests
+  // from the tail (back to the front of the queue, in order) until it does.
   Group G;
-  bool ok = wsb > 0 && s->dev.used() + s->data_in_flight + data + wsb <= s->budget &&
-            s->dev.alloc(wsb, &G.ws_off);
-  if (ok && !s->pin.alloc(upb + infob + 256, &G.pin_off)) {
-    s->dev.release(G.ws_off, wsb);
-    ok = false;
+  size_t wsb = 0, upb = 0, infob = 0;
+  for (;;) {
+    infob = (probs.size() * 2 * sizeof(int32_t) + 255) / 256 * 256;
+    for (auto& p : probs) p.info = reinterpret_cast<int32_t*>(s->dev_base);  // placeholder for sizing
+    wsb = ql_batch_workspace_bytes((int32_t)probs.size(), probs.data());
+    upb = batch_plan_upload_bytes((int32_t)probs.size(), probs.data());
+    bool fits = wsb > 0 && s->dev.used() + s->data_in_flight + data + wsb + infob <= s->budget &&
+                s->dev.alloc(wsb + infob, &G.ws_off);
+    if (fits && s->pin.alloc(upb + infob + 256, &G.pin_off)) break;
+    if (fits) s->dev.release(G.ws_off, wsb + infob);
+    Req& q = s->reqs[group.back()];
+    s->dev.release(q.out_off, q.out_bytes);
+    data -= q.data_bytes;
+    s->queue.push_front(group.back());
+    group.pop_back();
+    probs.pop_back();
+    if (group.empty()) return false;
   }
-  if (!ok) {  // not enough memory now: requeue at the front, in order
-    for (auto it = group.rbegin(); it != group.rend(); ++it) {
-      Req& q = s->reqs[*it];
-      s->dev.release(q.out_off, q.out_bytes);
-      s->queue.push_front(*it);
-    }
-    return false;
-  }
-  G.ws_bytes = wsb;
+  int32_t* info_dev = reinterpret_cast<int32_t*>(s->dev_base + G.ws_off + wsb);
+  for (size_t i = 0; i < probs.size(); ++i) probs[i].info = info_dev + 2 * i;
+  G.ws_bytes = wsb + infob;
   G.pin_bytes = upb + infob + 256;
   G.data_bytes = data;
   G.tickets = group;
-  cudaStream_t st = s->streams[s->next_stream];
-  s->next_stream = (s->next_stream + 1) % (int)s->streams.size();
+  G.stream = sidx;
+  cudaStream_t st = s->streams[sidx];
+  s->stream_busy[sidx] = 1;
   unsigned char* pin = s->pin_base + G.pin_off;
   int32_t* info_host = reinterpret_cast<int32_t*>(pin + (upb + 255) / 256 * 256);
   ql_status st1 = batch_prepare_async((int32_t)probs.size(), probs.data(), s->dev_base + G.ws_off, wsb, st, pin, upb);
   ql_status st2 = st1 == QL_OK ? ql_batch_launch(s->dev_base + G.ws_off, st) : st1;
+  if (st2 == QL_OK)
+    cudaMemcpyAsync(info_host, info_dev, probs.size() * 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
   for (size_t i = 0; i < group.size(); ++i) {
     Req& q = s->reqs[group[i]];
     q.state = 1;
     q.info_host = info_host + 2 * i;
-    if (st2 == QL_OK)
-      cudaMemcpyAsync(q.info_host, probs[i].info, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
-    else
-      q.info_host[0] = st2, q.info_host[1] = 0;
+    if (st2 != QL_OK) q.info_host[0] = st2, q.info_host[1] = 0;
   }
+  G.t_launch = now_s();
   cudaEventCreateWithFlags(&G.ev, cudaEventDisableTiming);
   cudaEventRecord(G.ev, st);
   s->inflight_reqs += (int64_t)group.size();
@@ -276,6 +310,7 @@ ql_server* ql_server_create(size_t hbm_budget_bytes, int32_t max_slots, int32_t 
     cudaStream_t st;
     cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
     s->streams.push_back(st);
+    s->stream_busy.push_back(0);
   }
   s->worker = std::thread(worker_main, s);
   return s;

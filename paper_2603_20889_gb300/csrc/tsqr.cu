@@ -5,9 +5,19 @@
 // completes the root writes R (or solves the least-squares problem of [A b]).  When the
 // double-float launch finds data outside its exponent range it leaves R unwritten and
 // raises a flag; the FP64 launch queued behind it runs only in that case.
+#include <cstdlib>
+
 #include "tsqr_launch.cuh"
 
 namespace ql {
+
+int tsqr_variant() {
+  static const int v = [] {
+    const char* e = std::getenv("QL_TSQR_CFG");
+    return e ? std::atoi(e) : 0;
+  }();
+  return v;
+}
 
 int device_sm_count() {
   static int sms = 0;

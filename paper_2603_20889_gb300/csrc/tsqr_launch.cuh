@@ -116,6 +116,28 @@ ql_status launch_one(const TsqrCall& c, const TreeView& tv_in, int gated) {
 template <typename S, typename Ar>
 ql_status dispatch(const TsqrCall& c, const TreeView& tv, int gated) {
   const int n = c.n;
+  if constexpr (std::is_same<S, double>::value && std::is_same<Ar, ArithDF>::value) {
+    const int v = tsqr_variant();  // alternative thread layouts (tuning experiments)
+    if (v > 0 && n > 4) {
+      if (n <= 8) {
+        if (v == 1) return launch_one<8, 1, 4, 256, S, Ar>(c, tv, gated);
+        if (v == 2) return launch_one<8, 2, 8, 256, S, Ar>(c, tv, gated);
+        if (v == 3) return launch_one<8, 2, 4, 128, S, Ar>(c, tv, gated);
+      } else if (n <= 16) {
+        if (v == 1) return launch_one<16, 2, 4, 256, S, Ar>(c, tv, gated);
+        if (v == 2) return launch_one<16, 4, 8, 256, S, Ar>(c, tv, gated);
+        if (v == 3) return launch_one<16, 1, 4, 128, S, Ar>(c, tv, gated);
+      } else if (n <= 32) {
+        if (v == 1) return launch_one<32, 4, 4, 256, S, Ar>(c, tv, gated);
+        if (v == 2) return launch_one<32, 8, 8, 256, S, Ar>(c, tv, gated);
+        if (v == 3) return launch_one<32, 2, 4, 128, S, Ar>(c, tv, gated);
+      } else {
+        if (v == 1) return launch_one<64, 8, 4, 256, S, Ar>(c, tv, gated);
+        if (v == 2) return launch_one<64, 16, 8, 256, S, Ar>(c, tv, gated);
+        if (v == 3) return launch_one<64, 4, 4, 128, S, Ar>(c, tv, gated);
+      }
+    }
+  }
   if (n <= 1) return launch_one<1, 1, 32, 128, S, Ar>(c, tv, gated);
   if (n <= 2) return launch_one<2, 1, 32, 128, S, Ar>(c, tv, gated);
   if (n <= 4) return launch_one<4, 1, 16, 128, S, Ar>(c, tv, gated);

@@ -184,6 +184,8 @@ def serving_stream(count: int = 20000, rate_per_s: float = 2000.0, seed: int = 5
         n = int(rng.integers(n_lo, n_hi + 1))
         dtype = "f32" if rng.uniform() < frac_f32 else "f64"
         kind = "lstsq" if rng.uniform() < frac_lstsq else "qr"
+        if kind == "lstsq":
+            n = min(n, n_hi - 1)  # [A b] has n + 1 <= n_hi columns
         kappa = float(math.exp(rng.uniform(0.0, math.log(kappa_hi))))
         out.append(Request(max(m, n + 1), n, kappa, seed * 1000003 + k, dtype, kind, t))
     return out

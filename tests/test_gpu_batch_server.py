@@ -197,3 +197,24 @@ def test_server_rejects_over_budget_and_bad_requests():
     assert st == q.QL_ERR_UNKNOWN
     assert srv.stats().rejected == 1
     srv.close()
+
+
+def test_server_completes_when_the_budget_is_the_limit():
+    """Requests whose data exceed the HBM budget many times over still all complete: the
+    server admits what fits, shrinks a group until its workspace fits, and never stalls."""
+    import paper_2603_20889_gb300 as q
+
+    m, n = 1 << 18, 10  # 21 MB per request
+    X = torch.randn((n, m), dtype=torch.float64, device="cuda")
+    srv = q.Server(128 << 20, 4096, 2)  # room for ~4 requests' data at a time
+    tickets = [srv.submit(q.Request(m=m, n=n, ld=m, X=X.data_ptr(), dtype=q.QL_F64, kind=0, b=None,
+                                    kappa_hint=1.0)) for _ in range(40)]
+    assert srv.drain(60.0) == 0
+    st = srv.stats()
+    assert st.completed == 40
+    assert st.hbm_peak_bytes <= 128 << 20
+    R0 = None
+    for t in tickets:
+        s, r = srv.poll(t)
+        assert s == 0 and r.status == 0
+    srv.close()
