@@ -33,12 +33,14 @@ sys.path.insert(0, ROOT)
 
 M = 1 << 25
 NS = [1, 2, 4, 8, 16, 32, 64]
+LS_M, LS_N = 1 << 24, 31  # least-squares [A b] workload
 KAPPA = 1e4
 METHODS = ["tsqr", "cholqr2", "svqb2"]
 PASSES = {"tsqr": 1, "cholqr2": 2, "svqb2": 2}
 METRIC = "Q-less QR effective GB/s (8mn B/time)"
 WORKLOAD = ("Q-less QR condition sweep: X = G S, m = 2^25 rows, n in {1,2,4,8,16,32,64}, kappa = 1e4, "
-            "FP64 storage; TSQR + Cholesky-QR2 + SVQB2 per n")
+            "FP64 storage; TSQR + Cholesky-QR2 + SVQB2 per n; plus least squares via the QR of [A b], "
+            "A 2^24 x 31 (kappa 1e3), FP64- and FP32-stored")
 
 
 def parse():
@@ -145,7 +147,6 @@ def run_ours(args, rank, world, local_rank):
     wsb = max(lib.ql_workspace_bytes(q.QL_AUTO, M, n, q.QL_F64) for n in NS)
     ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
     Rb = {n: torch.empty((n, n), dtype=torch.float64, device=dev) for n in NS}
-    info = torch.zeros((len(NS) * len(METHODS), 2), dtype=torch.int32, device=dev)
 
     def call(method, n, X, R, inf):
         ptr = X.data_ptr()
@@ -160,15 +161,45 @@ def run_ours(args, rank, world, local_rank):
         if st != 0:
             raise RuntimeError(f"{method} n={n}: status {st}")
 
-    calls = [(meth, n) for n in NS for meth in METHODS]
+    calls = [(meth, n) for n in NS for meth in METHODS] + [("lstsq_f64", LS_N), ("lstsq_f32", LS_N)]
+    # least squares through the QR of [A b]: A 2^24 x 31 (kappa 1e3), b = A x* + 1e-6 noise,
+    # FP64- and FP32-stored
+    import numpy as np
+
+    At = synth.conditioned_device(LS_M, LS_N, 1e3, seed=4242, device=dev)
+    xs = torch.from_numpy(np.random.default_rng(4243).standard_normal(LS_N)).to(dev)
+    g = torch.Generator(device=dev)
+    g.manual_seed(4244)
+    bvec = xs @ At + 1e-6 * torch.randn(LS_M, generator=g, device=dev, dtype=torch.float64)
+    ls = {"lstsq_f64": (At, bvec, q.QL_F64), "lstsq_f32": (At.float(), bvec.float(), q.QL_F32)}
+    xout = torch.empty(LS_N + 1, dtype=torch.float64, device=dev)
+
+    def call_ls(name, inf):
+        A, b, dt = ls[name]
+        st = lib.ql_lstsq_qless(LS_M, LS_N, A.data_ptr(), LS_M, b.data_ptr(), dt, q.QL_TSQR, xout.data_ptr(),
+                                xout[LS_N:].data_ptr(), None, inf.data_ptr(), ws.data_ptr(), wsb, sptr)
+        if st != 0:
+            raise RuntimeError(f"{name}: status {st}")
+
+    def nbytes(meth, n):
+        if meth == "lstsq_f64":
+            return 8.0 * LS_M * (n + 1)
+        if meth == "lstsq_f32":
+            return 4.0 * LS_M * (n + 1)
+        return 8.0 * M * n
+
     evs = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in calls]
            for _ in range(args.steps)]
+    info = torch.zeros((len(calls), 2), dtype=torch.int32, device=dev)
 
     def step(ev=None):
         for i, (meth, n) in enumerate(calls):
             if ev:
                 ev[i][0].record(stream)
-            call(meth, n, Xs[n], Rb[n], info[i])
+            if meth.startswith("lstsq"):
+                call_ls(meth, info[i])
+            else:
+                call(meth, n, Xs[n], Rb[n], info[i])
             if ev:
                 ev[i][1].record(stream)
 
@@ -204,7 +235,7 @@ def run_ours(args, rank, world, local_rank):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         total_ms = float(t.item())
 
-    bytes_step = sum(8.0 * M * n for (_, n) in calls)
+    bytes_step = sum(nbytes(meth, n) for (meth, n) in calls)
     ms_step = total_ms / args.steps
     value = world * bytes_step * args.steps / (total_ms / 1e3) / 1e9
 
@@ -213,23 +244,23 @@ def run_ours(args, rank, world, local_rank):
     sweep = []
     for i, (meth, n) in enumerate(calls):
         ms = per_call[i] / args.steps
-        sweep.append({"method": meth, "n": n, "ms": round(ms, 4), "eff_gbs": round(8.0 * M * n / ms / 1e6, 1),
-                      "alg_gbs": round(PASSES[meth] * 8.0 * M * n / ms / 1e6, 1)})
+        sweep.append({"method": meth, "n": n, "ms": round(ms, 4), "eff_gbs": round(nbytes(meth, n) / ms / 1e6, 1),
+                      "alg_gbs": round(PASSES.get(meth, 1) * nbytes(meth, n) / ms / 1e6, 1)})
     dom = max(range(len(calls)), key=lambda i: per_call[i])
     dmeth, dn = calls[dom]
     dms = per_call[dom] / args.steps
-    launches_per_call = 2 if dmeth == "tsqr" else 4  # kernels incl. the gated FP64 launches
-    # the timed share of the dominant kernel: one pass = one launch reading 8 m n bytes
-    kern_ms = dms / PASSES[dmeth]
-    achieved = 8.0 * M * dn / kern_ms / 1e6
+    # the timed share of the dominant kernel: one pass = one launch reading its bytes
+    kern_ms = dms / PASSES.get(dmeth, 1)
+    achieved = nbytes(dmeth, dn) / kern_ms / 1e6
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": None, "peak_source": peak_kind,
                 "kernel": f"{'tsqr_kernel' if dmeth == 'tsqr' else 'gram_kernel'} ({dmeth}, n={dn}, m=2^25)",
-                "algorithmic_bytes_per_launch": 8 * M * dn,
+                "algorithmic_bytes_per_launch": int(nbytes(dmeth, dn)),
                 "note": "per-launch time from CUDA events around the call on its stream; Gram methods: "
                         "call time / 2 passes"}
 
-    e2e = run_e2e(args, q, lib, torch, dev, Xs, ws, wsb, stream) if args.e2e_steps > 0 else None
+    e2e = run_e2e(args, q, lib, torch, dev, Xs, ws, wsb, stream, ls) if args.e2e_steps > 0 else None
+    del ls, At, bvec
     del Xs
     torch.cuda.empty_cache()
     extra = {}
@@ -262,7 +293,7 @@ def run_ours(args, rank, world, local_rank):
     return out
 
 
-def run_e2e(args, q, lib, torch, dev, Xs, ws, wsb, stream):
+def run_e2e(args, q, lib, torch, dev, Xs, ws, wsb, stream, ls):
     """The same sweep through the C ABI from HOST buffers: every step copies each X from
     pinned host memory to the device (on a copy stream, double-buffered so that the copy of
     the next matrix overlaps the factorisations of the current one) and reads every R back,
@@ -281,8 +312,14 @@ def run_e2e(args, q, lib, torch, dev, Xs, ws, wsb, stream):
     cstream = _t.cuda.Stream(device=dev)
     copied = [_t.cuda.Event(), _t.cuda.Event()]
     used = [_t.cuda.Event(), _t.cuda.Event()]
-    h2d = sum(host[n].numel() * 8 for n in NS)
-    d2h = sum(Rh[n].numel() * 8 * len(METHODS) for n in NS)
+    hls = {k: (_t.empty(A.shape, dtype=A.dtype, pin_memory=True).copy_(A),
+               _t.empty(b.shape, dtype=b.dtype, pin_memory=True).copy_(b), _t.empty_like(A), _t.empty_like(b), dt)
+           for k, (A, b, dt) in ls.items()}
+    xh = _t.empty(LS_N + 1, dtype=_t.float64, pin_memory=True)
+    xd = _t.empty(LS_N + 1, dtype=_t.float64, device=dev)
+    h2d = sum(host[n].numel() * 8 for n in NS) + sum(v[0].numel() * v[0].element_size() + v[1].numel() *
+                                                     v[1].element_size() for v in hls.values())
+    d2h = sum(Rh[n].numel() * 8 * len(METHODS) for n in NS) + len(hls) * (LS_N + 1) * 8
     seq = [0]
 
     def step():
@@ -307,6 +344,12 @@ def run_e2e(args, q, lib, torch, dev, Xs, ws, wsb, stream):
                                       ws.data_ptr(), wsb, sptr)
                 Rh[n].copy_(Rd[n], non_blocking=True)
             used[b].record(stream)
+        for name, (Ah, bh, Ad, bd, dt) in hls.items():  # least squares: [A b] from host, x back
+            Ad.copy_(Ah, non_blocking=True)
+            bd.copy_(bh, non_blocking=True)
+            lib.ql_lstsq_qless(LS_M, LS_N, Ad.data_ptr(), LS_M, bd.data_ptr(), dt, q.QL_TSQR, xd.data_ptr(),
+                               xd[LS_N:].data_ptr(), None, inf.data_ptr(), ws.data_ptr(), wsb, sptr)
+            xh.copy_(xd, non_blocking=True)
 
     step()
     _t.cuda.synchronize()
@@ -319,8 +362,8 @@ def run_e2e(args, q, lib, torch, dev, Xs, ws, wsb, stream):
     e1.record(stream)
     _t.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.e2e_steps
-    bytes_step = sum(8.0 * M * n * len(METHODS) for n in NS)
-    del host, bufs
+    bytes_step = sum(8.0 * M * n * len(METHODS) for n in NS) + 12.0 * LS_M * (LS_N + 1)
+    del host, bufs, hls
     return {"value": round(bytes_step / (ms / 1e3) / 1e9, 2), "unit": "GB/s", "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h), "ms_per_step": round(ms, 3),
             "note": "each X copied host->device once per step from pinned memory on a second stream "

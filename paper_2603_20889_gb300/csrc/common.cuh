@@ -219,6 +219,10 @@ QL_DEV void cp_async_4(void* smem, const void* gmem, bool valid) {
 }
 QL_DEV void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 QL_DEV void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+template <int N>
+QL_DEV void cp_async_wait_group() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
 
 template <typename S>
 QL_DEV void cp_async_elem(S* smem, const S* gmem, bool valid);

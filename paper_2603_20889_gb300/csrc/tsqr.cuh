@@ -41,6 +41,10 @@ struct TsqrShape {
   static constexpr int TR = T / TC;        // row threads per column group
   static constexpr int NCT = NC / TC;      // columns held by one thread
   static constexpr int B = TR * RPT;       // rows per tile
+  // staging depth: one buffer (the next tile lands while the current one is factored from
+  // registers).  Deeper staging was measured slower for narrow X: the extra shared memory
+  // costs CTAs per SM, and with them the latency hiding that more stages would add.
+  static constexpr int STAGES = 1;
   static_assert(NC % TC == 0, "column groups must divide NC");
   static_assert(TR % 16 == 0 || TR == T, "row threads per group must be a multiple of 16");
 };
@@ -50,9 +54,10 @@ template <int NC, int TC, int RPT, int T, typename S, typename Ar>
 struct TsqrSmem {
   using Sh = TsqrShape<NC, TC, RPT, T>;
   using V = typename Ar::T;
-  static constexpr size_t kStage = sizeof(S) * NC * Sh::B;           // staged tile
+  static constexpr size_t kStage = sizeof(S) * NC * Sh::B;           // one staged tile
+  static constexpr size_t kStages = kStage * Sh::STAGES;
   static constexpr size_t kMerge = sizeof(double) * 2 * NC * NC;     // [Ra; Rb]
-  static constexpr size_t kArena = kStage > kMerge ? kStage : kMerge;
+  static constexpr size_t kArena = kStages > kMerge ? kStages : kMerge;
   static constexpr size_t kR = sizeof(V) * NC * NC;                  // running triangle
   static constexpr size_t kPart = sizeof(V) * NC * Sh::TR;           // column partial sums
   static constexpr size_t kPiv = (TC > 1) ? sizeof(V) * Sh::B : 0;   // pivot broadcast
@@ -130,9 +135,11 @@ struct TsqrCta {
     for (int i = tid; i < NC; i += T) colmax[i] = 0;
   }
 
-  // Issue the cp.async copies of rows [row0, row0 + B) of all NC columns into the stage.
-  QL_DEV void issue_tile(const TsqrProblem<S>& p, int64_t row0) {
+  // Issue the cp.async copies of rows [row0, row0 + B) of all NC columns into stage
+  // buffer `buf` (one commit group per tile).
+  QL_DEV void issue_tile(const TsqrProblem<S>& p, int64_t row0, int buf = 0) {
     constexpr int PER = B / T > 0 ? B / T : 1;
+    S* st = stage + (size_t)buf * NC * B;
 #pragma unroll 1
     for (int c = 0; c < NC; ++c) {
       const S* col = p.src.col(c < p.n ? c : 0);
@@ -143,7 +150,7 @@ struct TsqrCta {
         if (B % T == 0 || r < B) {
           int64_t row = row0 + r;
           bool v = cvalid && row < p.m;
-          cp_async_elem<S>(stage + c * B + r, v ? col + row : col, v);
+          cp_async_elem<S>(st + c * B + r, v ? col + row : col, v);
         }
       }
     }
@@ -153,7 +160,8 @@ struct TsqrCta {
   // Stage -> registers (with the range bookkeeping of the double-float policy: the
   // column's largest exponent is reduced over the lanes that share the column, then one
   // shared-memory atomic per column and warp records it).
-  QL_DEV void stage_to_regs(V (&w)[RPT][NCT]) {
+  QL_DEV void stage_to_regs(V (&w)[RPT][NCT], int buf = 0) {
+    const S* stage = this->stage + (size_t)buf * NC * B;
     constexpr unsigned kHalf = TR >= 32 ? 0xffffffffu : 0x0000ffffu;
     const unsigned gmask = TR >= 32 ? 0xffffffffu : (((tid & 31) < 16) ? kHalf : (kHalf << 16));
 #pragma unroll
@@ -293,18 +301,30 @@ struct TsqrCta {
 
   // Process tiles [t0, t1) of problem p (tile t covers rows [row_base + t*B, ...)).
   QL_DEV void run(const TsqrProblem<S>& p, int64_t row_base, int64_t t0, int64_t t1) {
+    constexpr int ST = Sh::STAGES;
     V w[RPT][NCT];
     if (t0 >= t1) return;
-    issue_tile(p, row_base + t0 * B);
+#pragma unroll
+    for (int s = 0; s < ST; ++s) {  // prologue: ST tiles in flight (empty groups past the end)
+      if (t0 + s < t1)
+        issue_tile(p, row_base + (t0 + s) * B, s);
+      else
+        cp_async_commit();
+    }
     for (int64_t t = t0; t < t1; ++t) {
-      cp_async_wait_all();
+      const int buf = (int)((t - t0) % ST);
+      cp_async_wait_group<ST - 1>();  // this tile's group has landed
       __syncthreads();
-      stage_to_regs(w);
+      stage_to_regs(w, buf);
       for (int i = tid; i < NC; i += T) cn[i] = Ar::zero();
       __syncthreads();
-      if (t + 1 < t1) issue_tile(p, row_base + (t + 1) * B);
+      if (t + ST < t1)
+        issue_tile(p, row_base + (t + ST) * B, buf);
+      else
+        cp_async_commit();
       factor_tile(w, p.n);
     }
+    cp_async_wait_all();
     __syncthreads();
   }
 
