@@ -65,6 +65,27 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+# ------------------------------------------------------------------ multi-rank aggregation
+
+
+def max_over_ranks(x: float, device=None) -> float:
+    """Largest value of x over all ranks (identity without torch.distributed)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_gbs(bytes_per_step: float, steps: int, world: int, max_ms: float) -> float:
+    """Whole-job throughput: every rank processed bytes_per_step per step (weak scaling);
+    the job took the slowest rank's time."""
+    return world * bytes_per_step * steps / (max_ms / 1e3) / 1e9
+
+
 # ------------------------------------------------------------------ clocks
 
 
@@ -228,16 +249,12 @@ def run_ours(args, rank, world, local_rank):
     launches = lib.ql_launch_count() - l0
     if world > 1:
         torch.distributed.barrier()
-    total_ms = t_start.elapsed_time(t_end)
+    total_ms = max_over_ranks(t_start.elapsed_time(t_end), dev)
     clk = clocks.stop()
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
 
     bytes_step = sum(nbytes(meth, n) for (meth, n) in calls)
     ms_step = total_ms / args.steps
-    value = world * bytes_step * args.steps / (total_ms / 1e3) / 1e9
+    value = whole_job_gbs(bytes_step, args.steps, world, total_ms)
 
     # dominant call (largest share of the step) and its roofline (HBM, algorithmic bytes)
     peak, peak_kind = measured_peaks()
