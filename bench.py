@@ -53,6 +53,8 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--no-batched", dest="batched", action="store_false")
     p.add_argument("--no-serving", dest="serving", action="store_false")
+    p.add_argument("--case", default=None,
+                   help="METHOD:N:M -- time one call shape alone (profiling aid; prints its own JSON line)")
     return p.parse_args()
 
 
@@ -593,6 +595,38 @@ def cpu_baseline(seconds):
             "sample": f"row samples of the same sweep ({s:.1f} s of CPU): {sample}"}
 
 
+# ------------------------------------------------------------------ one call shape
+
+
+def run_case(spec: str, reps: int = 3) -> dict:
+    """One call shape of the sweep (METHOD:N:M), run reps times after one warm-up call:
+    the small, self-contained program that kernel profiles are taken on."""
+    import torch
+
+    import paper_2603_20889_gb300 as q
+    from paper_2603_20889_gb300 import synth
+
+    method, n, m = spec.split(":")
+    n, m = int(n), int(m)
+    q.load_library()
+    X = synth.conditioned_device(m, n, KAPPA, seed=n).T
+    ws = q.workspace(q.QL_AUTO, m, n, q.QL_F64)
+    R = torch.empty((n, n), dtype=torch.float64, device="cuda").T
+    info = torch.zeros(2, dtype=torch.int32, device="cuda")
+    call = {"tsqr": lambda: q.tsqr_qless(X, R, info, ws), "cholqr2": lambda: q.cholqr2_qless(X, R, info, ws),
+            "svqb2": lambda: q.svqb_qless(X, R, None, 0.0, info, ws)}[method]
+    call()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        call()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    return {"case": spec, "ms": round(ms, 3), "eff_gbs": round(8 * m * n / ms / 1e6, 1), "info": info.tolist()}
+
+
 # ------------------------------------------------------------------ main
 
 
@@ -601,6 +635,9 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.case:
+        print(json.dumps(run_case(args.case)))
+        return 0
     if args.impl == "reference":
         if rank != 0:
             return 0

@@ -19,7 +19,7 @@ static int nc_of(int n) { return n <= 1 ? 1 : n <= 2 ? 2 : n <= 4 ? 4 : n <= 8 ?
 
 static size_t gram_layout(int n, GramWs* w, void* base) {
   const int nc = nc_of(n);
-  const size_t head = 256;
+  const size_t head = 512;  // flags, counters and the first pass's column exponents
   const size_t keep = (size_t)3 * kMaxN * kMaxN * sizeof(double);
   const size_t parts = (size_t)device_sm_count() * kGramMaxCtasPerSm * nc * nc * sizeof(double);
   if (w && base) {
@@ -42,7 +42,7 @@ ql_status gram_launch(const GramCall& c, ql_arith arith) {
   if (!c.ws || c.ws_bytes < gram_layout(c.n, nullptr, nullptr)) return QL_ERR_WORKSPACE;
   GramWs w;
   gram_layout(c.n, &w, c.ws);
-  if (cudaMemsetAsync(w.flags, 0, 256, c.stream) != cudaSuccess) return QL_ERR_CUDA;
+  if (cudaMemsetAsync(w.flags, 0, 512, c.stream) != cudaSuccess) return QL_ERR_CUDA;
   ql_status st;
   if (c.dtype == QL_F64) {
     if (arith == QL_ARITH_F64) return gram_dispatch<double, ArithF64>(c, w, 0);

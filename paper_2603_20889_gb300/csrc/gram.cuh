@@ -36,7 +36,7 @@ struct GramSmem {
   static constexpr size_t kRed = sizeof(V) * Sh::SL * Sh::NBT * Sh::BS * Sh::BS;
   static constexpr size_t kYY = 2 * kY > kRed ? 2 * kY : kRed;  // Y0, Y1 (or the slice reduction)
   static constexpr size_t kM = sizeof(V) * NC * NC;
-  static constexpr size_t kEpi = sizeof(double) * (5 * NC * NC + 8 * NC);  // n x n FP64 workspace
+  static constexpr size_t kEpi = sizeof(double) * (5 * NC * (NC + 1) + 8 * (NC + 1));  // n x n FP64, ld NC + 1
   static constexpr size_t kOffY = (kStage + 15) / 16 * 16;
   static constexpr size_t kOffM = kOffY + kYY;
   static constexpr size_t kOffMisc = kOffM + kM;

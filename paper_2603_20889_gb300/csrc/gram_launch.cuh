@@ -15,7 +15,8 @@ namespace ql {
 constexpr int kGramMaxCtasPerSm = 4;
 
 struct GramWs {
-  int* flags;        // [0] range, [1] first-pass breakdown, [2] arrival counter pass 1, [3] pass 2
+  int* flags;        // [0] range, [1] first-pass breakdown, [2] arrival counter pass 1, [3] pass 2,
+                    // [64 + c]: largest biased exponent of column c over all rows (tensor-core pass 1)
   double* keep;      // 3 n x n blocks carried from pass 1 to pass 2 (row-major, ld n)
   double* partials;  // one NC x NC partial Gram per CTA
 };
@@ -235,13 +236,15 @@ QL_DEV void gram_finish(const GramArgs<S>& a, unsigned char* smem, const int* co
   __threadfence();
   if (Ar::kRangeChecked && *(volatile int*)&a.w.flags[0] != 0) return;  // the FP64 launches redo it
 
-  // ---------------- epilogue: one CTA, FP64, shared memory reused from here on
-  double* Cs = reinterpret_cast<double*>(smem);  // n x n, ld NC
-  double* Us = Cs + NC * NC;
-  double* Ps = Us + NC * NC;
-  double* Qs = Ps + NC * NC;
-  double* vec = Qs + NC * NC;  // 8 NC
-  int* sflag = reinterpret_cast<int*>(vec + 8 * NC);
+  // ---------------- epilogue: one CTA, FP64, shared memory reused from here on; the odd
+  // leading dimension keeps column walks (Jacobi rotations) free of bank conflicts
+  constexpr int LE = NC + 1;
+  double* Cs = reinterpret_cast<double*>(smem);  // n x n, ld LE
+  double* Us = Cs + NC * LE;
+  double* Ps = Us + NC * LE;
+  double* Qs = Ps + NC * LE;
+  double* vec = Qs + NC * LE;  // 8 LE doubles
+  int* sflag = reinterpret_cast<int*>(vec + 8 * LE);
   __syncthreads();
   for (int e = tid; e < n * n; e += T) {
     int p = e / n, q = e % n;
@@ -252,14 +255,14 @@ QL_DEV void gram_finish(const GramArgs<S>& a, unsigned char* smem, const int* co
       s = Ar::add(s, Ar::load(__ldcg(a.w.partials + (size_t)b * NC * NC + p * NC + q), E));
     }
     double v = Ar::to_double(s);
-    Cs[p * NC + q] = v;
-    Cs[q * NC + p] = v;
+    Cs[p * LE + q] = v;
+    Cs[q * LE + p] = v;
   }
   __syncthreads();
   double* keep = a.w.keep;  // [0]: R1 or S1, [1]: M (R1^{-1} or B1)
   const int nn = n * n;
   if (a.method == QL_CHOLQR2) {
-    int fail = chol_upper_inplace<T>(Cs, NC, n, sflag);
+    int fail = chol_upper_inplace<T>(Cs, LE, n, sflag);
     if (fail) {
       if (a.pass == 1) a.w.flags[1] = 1;
       write_nan_outputs(a, T);
@@ -267,55 +270,55 @@ QL_DEV void gram_finish(const GramArgs<S>& a, unsigned char* smem, const int* co
       return;
     }
     if (a.pass == 1) {
-      tri_upper_inverse<T>(Cs, NC, Us, NC, n);
+      tri_upper_inverse<T>(Cs, LE, Us, LE, n);
       for (int e = tid; e < nn; e += T) {
-        keep[e] = Cs[(e / n) * NC + e % n];
-        keep[nn + e] = Us[(e / n) * NC + e % n];
+        keep[e] = Cs[(e / n) * LE + e % n];
+        keep[nn + e] = Us[(e / n) * LE + e % n];
       }
       return;
     }
     // pass 2: R = R2 R1
-    for (int e = tid; e < nn; e += T) Us[(e / n) * NC + e % n] = __ldcg(keep + e);
+    for (int e = tid; e < nn; e += T) Us[(e / n) * LE + e % n] = __ldcg(keep + e);
     __syncthreads();
-    upper_times_upper<T>(Cs, NC, Us, NC, Ps, NC, n);
+    upper_times_upper<T>(Cs, LE, Us, LE, Ps, LE, n);
   } else {
-    jacobi_eig<T>(Cs, NC, Us, NC, n, vec, sflag);
+    jacobi_eig<T>(Cs, LE, Us, LE, n, vec, sflag);
     // lambda_max and the truncation threshold
     double lmax = 0.0;
-    for (int i = 0; i < n; ++i) lmax = fmax(lmax, Cs[i * NC + i]);
+    for (int i = 0; i < n; ++i) lmax = fmax(lmax, Cs[i * LE + i]);
     double tol = a.rank_tol > 0.0 ? a.rank_tol : (double)n * 2.220446049250313e-16;
     double cut = tol * lmax;
     if (a.pass == 1) {
       for (int e = tid; e < nn; e += T) {
         int r = e / n, i = e % n;  // B1(r, i) = U(r, i) lambda_i^{-1/2};  S1(i, r) = lambda_i^{1/2} U(r, i)
-        double li = Cs[i * NC + i];
+        double li = Cs[i * LE + i];
         bool keepit = li > cut && li > 0.0;
         double sq = keepit ? sqrt(li) : 0.0;
-        keep[nn + r * n + i] = keepit ? Us[r * NC + i] / sq : 0.0;
-        keep[i * n + r] = sq * Us[r * NC + i];
+        keep[nn + r * n + i] = keepit ? Us[r * LE + i] / sq : 0.0;
+        keep[i * n + r] = sq * Us[r * LE + i];
       }
       return;
     }
     // pass 2: Z = S2 S1 with S2(i, r) = lambda2_i^{1/2} U2(r, i);  R = qr_r(Z)
     for (int e = tid; e < nn; e += T) {
       int i = e / n, r = e % n;
-      double li = Cs[i * NC + i];
+      double li = Cs[i * LE + i];
       bool keepit = li > cut && li > 0.0;
-      Qs[i * NC + r] = (keepit ? sqrt(li) : 0.0) * Us[r * NC + i];
+      Qs[i * LE + r] = (keepit ? sqrt(li) : 0.0) * Us[r * LE + i];
     }
     __syncthreads();
-    for (int e = tid; e < nn; e += T) Us[(e / n) * NC + e % n] = __ldcg(keep + e);  // S1
+    for (int e = tid; e < nn; e += T) Us[(e / n) * LE + e % n] = __ldcg(keep + e);  // S1
     __syncthreads();
-    full_times_full<T>(Qs, NC, Us, NC, Ps, NC, n);
+    full_times_full<T>(Qs, LE, Us, LE, Ps, LE, n);
     if (a.Z && a.epilogue == kEpiR)
-      for (int e = tid; e < nn; e += T) a.Z[(e / n) * n + e % n] = Ps[(e % n) * NC + e / n];  // column-major
+      for (int e = tid; e < nn; e += T) a.Z[(e / n) * n + e % n] = Ps[(e % n) * LE + e / n];  // column-major
     __syncthreads();
-    householder_square<T>(Ps, NC, n, vec);
+    householder_square<T>(Ps, LE, n, vec);
   }
   if (a.epilogue == kEpiR)
-    epilogue_r<T>(Ps, NC, n, a.R, a.ldr, a.info, sflag);
+    epilogue_r<T>(Ps, LE, n, a.R, a.ldr, a.info, sflag);
   else
-    epilogue_lstsq<T>(Ps, NC, n, a.x, a.resnorm, a.Rext, a.info, vec, sflag);
+    epilogue_lstsq<T>(Ps, LE, n, a.x, a.resnorm, a.Rext, a.info, vec, sflag);
 }
 
 
@@ -328,6 +331,9 @@ __global__ void __launch_bounds__(256, 1) gram_tc_kernel(GramArgs<S> a) {
   constexpr int T = 256, KT = Sh::KT, LDR = Sh::LDR, G = Sh::G, KS = Sh::KS, KPART = Sh::KPART;
   constexpr int GPR = Sh::NCB / G;              // column-block groups per row block
   constexpr int PAIRS = NC * KT / 2 / T;        // row pairs per thread and tile
+  constexpr int LDY = Sm::LDY;
+  constexpr int KSTEPS = NC / 16;               // 16-wide k-steps of Y = X M'
+  constexpr int WPC = 8 / Sh::NCB;              // warps per 8-column block of Y
   extern __shared__ __align__(16) unsigned char smem[];
   const int tid = threadIdx.x, n = a.n, lane = tid & 31, warp = tid >> 5;
 
@@ -337,26 +343,87 @@ __global__ void __launch_bounds__(256, 1) gram_tc_kernel(GramArgs<S> a) {
     return;
   }
   S* stage = reinterpret_cast<S*>(smem);
-  df* stage_df = reinterpret_cast<df*>(smem);
+  df* ydf = reinterpret_cast<df*>(smem);  // second pass: the Y tile, column c at c * LDY
   unsigned short* slices = reinterpret_cast<unsigned short*>(smem + Sm::kOffSlices);
-  df* Mv = reinterpret_cast<df*>(smem + Sm::kOffM);
   float* pow2c = reinterpret_cast<float*>(smem + Sm::kOffPow);
   int* expo = reinterpret_cast<int*>(smem + Sm::kOffExpo);
   int* colmax = reinterpret_cast<int*>(smem + Sm::kOffColmax);
+  int* gexp = reinterpret_cast<int*>(smem + Sm::kOffGexp);
   unsigned* zero16 = reinterpret_cast<unsigned*>(smem + Sm::kOffZero);
   int* misc = reinterpret_cast<int*>(smem + Sm::kOffMisc);
 
-  for (int i = tid; i < NC; i += T) colmax[i] = 0;
-  if (tid < 4) zero16[tid] = 0u;
-  if constexpr (XF != kXNone) {
-    const double* M = a.w.keep + (size_t)n * n;
-    for (int i = tid; i < NC * NC; i += T) {
-      int r = i / NC, c = i % NC;
-      Mv[i] = (r < n && c < n) ? df_from_double_rn(__ldcg(M + r * n + c)) : df{0.0f, 0.0f};
-    }
+  for (int i = tid; i < NC; i += T) {
+    colmax[i] = 0;
+    gexp[i] = (XF != kXNone && i < n) ? __ldcg(&a.w.flags[64 + i]) : 0;
   }
+  if (tid < 4) zero16[tid] = 0u;
+  __syncthreads();
   constexpr int U = Sh::U;
   const int g = lane >> 2, t4 = lane & 3;
+
+  // ---- second pass: this warp's 8-column block of Y and the B fragments of M' = diag(2^e_k) M
+  // Upper-triangular M' (Cholesky-QR2) needs k-steps 0..cbw/2 only; with NC = 64 the blocks
+  // are paired so that the two warps on one scheduler share 5 k-steps.
+  const int cbw = (NC == 64 && warp >= 4) ? 11 - warp : warp / WPC;
+  const int rpart = (NC == 64) ? 0 : warp % WPC;
+  const int ksw = XF == kXUpper ? (cbw >> 1) + 1 : KSTEPS;
+  unsigned bq[XF != kXNone ? KSTEPS : 1][7][2];
+  float ysc[2][7];  // 2^(f_j - 7(d + 2)) for this thread's two Y columns and the 7 weights
+  if constexpr (XF != kXNone) {
+    const double* M = a.w.keep + (size_t)n * n;  // pass-1 output, row-major, ld n
+    const int jb = cbw * 8 + g;
+    double mv[KSTEPS][4];
+    int F = 0;
+#pragma unroll
+    for (int ks = 0; ks < KSTEPS; ++ks)
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        const int k = 16 * ks + 2 * t4 + (h & 1) + 8 * (h >> 1);
+        double v = 0.0;
+        if (k < n && jb < n && (XF != kXUpper || k <= jb)) {
+          const int ek = gexp[k];
+          if (ek > 0) v = __ldcg(M + (size_t)k * n + jb) * __longlong_as_double((long long)(ek + 1) << 52);
+        }
+        mv[ks][h] = v;
+        F = max(F, (int)((__double_as_longlong(v) >> 52) & 0x7ff));
+      }
+    F = max(F, __shfl_xor_sync(0xffffffffu, F, 1));
+    F = max(F, __shfl_xor_sync(0xffffffffu, F, 2));  // max over column jb of M'
+#pragma unroll
+    for (int ks = 0; ks < KSTEPS; ++ks) {
+      unsigned long long N[4];
+      unsigned sg[4];
+#pragma unroll
+      for (int h = 0; h < 4; ++h) N[h] = fixed_of_double(mv[ks][h], F, sg[h]);
+#pragma unroll
+      for (int q = 0; q < 7; ++q) {
+        const int sh = 7 * (6 - q);
+        bq[ks][q][0] = bf16_digit((unsigned)(N[0] >> sh) & 127u, sg[0]) |
+                       (bf16_digit((unsigned)(N[1] >> sh) & 127u, sg[1]) << 16);
+        bq[ks][q][1] = bf16_digit((unsigned)(N[2] >> sh) & 127u, sg[2]) |
+                       (bf16_digit((unsigned)(N[3] >> sh) & 127u, sg[3]) << 16);
+      }
+    }
+    // the flush scale of this thread's Y columns cbw*8 + 2 t4 + h must stay a normal float
+    bool bad = false;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int Fj = __shfl_sync(0xffffffffu, F, 4 * (2 * t4 + h));
+      const int f = Fj - 1022;  // |M'(:, j)| < 2^f
+      if (Fj > 0 && (f < -70 || f > 100)) bad = true;
+#pragma unroll
+      for (int d = 0; d < 7; ++d) {
+        const int e = f - 7 * (d + 2);
+        ysc[h][d] = (Fj > 0 && !bad) ? __int_as_float((e + 127) << 23) : 0.0f;
+      }
+    }
+    if (__syncthreads_or(bad)) {  // out of the double-float range: the FP64 launches redo it
+      if (tid == 0) atomicOr(&a.w.flags[0], 1);
+      gram_finish<NC, T, S, ArithDF>(a, smem, colmax, misc);
+      return;
+    }
+  }
+
   df acc[U][G][4];  // persistent per-unit C accumulators
 #pragma unroll
   for (int ui = 0; ui < U; ++ui)
@@ -380,6 +447,34 @@ __global__ void __launch_bounds__(256, 1) gram_tc_kernel(GramArgs<S> a) {
     }
     cp_async_commit();
   };
+  // seven signed base-128 digits of the staged X per value, two rows per 32-bit store;
+  // ex[c] is the biased double exponent that bounds column c
+  auto slice_stage = [&](const int* ex) {
+#pragma unroll 4
+    for (int k2 = 0; k2 < PAIRS; ++k2) {
+      const int pi = tid + T * k2, c = (2 * pi) / KT, r = (2 * pi) % KT;
+      const int em = ex[c];
+      unsigned long long N[2];
+      unsigned sg[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        if constexpr (sizeof(S) == 8) {
+          N[h] = fixed_of_double((double)stage[c * KT + r + h], em, sg[h]);
+        } else {
+          float x = (float)stage[c * KT + r + h];
+          sg[h] = __float_as_uint(x) & 0x80000000u;
+          N[h] = em > 0 ? fixed_of_float(x, em - 896) : 0ull;
+        }
+      }
+#pragma unroll
+      for (int p = 0; p < Sh::ND; ++p) {
+        const int sh = 7 * (Sh::ND - 1 - p);
+        unsigned lo16 = bf16_digit((unsigned)(N[0] >> sh) & 127u, sg[0]);
+        unsigned hi16 = bf16_digit((unsigned)(N[1] >> sh) & 127u, sg[1]);
+        *reinterpret_cast<unsigned*>(slices + ((size_t)p * NC + c) * LDR + r) = lo16 | (hi16 << 16);
+      }
+    }
+  };
 
   if (t0 < t1) issue(t0);
   __syncthreads();
@@ -388,7 +483,6 @@ __global__ void __launch_bounds__(256, 1) gram_tc_kernel(GramArgs<S> a) {
     __syncthreads();
     for (int i = tid; i < NC; i += T) expo[i] = 0;
     __syncthreads();
-    df yv[XF != kXNone ? 2 * PAIRS : 1];
     if constexpr (XF == kXNone) {
       // column maxima of the biased double exponent (and the range record)
 #pragma unroll 4
@@ -410,101 +504,97 @@ __global__ void __launch_bounds__(256, 1) gram_tc_kernel(GramArgs<S> a) {
           atomicMax(&colmax[c], (int)em);
         }
       }
-    } else {
-      if constexpr (sizeof(S) == 8) {
-        // convert the stage in place to double-float, once per element (+ range record)
-#pragma unroll 4
-        for (int k2 = 0; k2 < PAIRS; ++k2) {
-          const int pi = tid + T * k2, c = (2 * pi) / KT, r = (2 * pi) % KT;
-          int E0, E1;
-          df d0 = Ar::load((double)stage[c * KT + r], E0);
-          df d1 = Ar::load((double)stage[c * KT + r + 1], E1);
-          stage_df[c * KT + r] = d0;
-          stage_df[c * KT + r + 1] = d1;
-          unsigned em = __reduce_max_sync(0xffffffffu, (unsigned)max(E0, E1));
-          if (lane == 0 && em > 0) atomicMax(&colmax[c], (int)em);
-        }
-      } else {
-#pragma unroll 4
-        for (int k2 = 0; k2 < PAIRS; ++k2) {
-          const int pi = tid + T * k2, c = (2 * pi) / KT, r = (2 * pi) % KT;
-          unsigned e0 = (__float_as_uint((float)stage[c * KT + r]) >> 23) & 0xff;
-          unsigned e1 = (__float_as_uint((float)stage[c * KT + r + 1]) >> 23) & 0xff;
-          unsigned em = __reduce_max_sync(0xffffffffu, max(e0 ? e0 + 896 : 0u, e1 ? e1 + 896 : 0u));
-          if (lane == 0 && em > 0) atomicMax(&colmax[c], (int)em);
-        }
-      }
       __syncthreads();
-      // Y = W M, one pair of rows of one column per step (unrolled: yv stays in registers)
+      // per-column scale 2^e_c, |x| < 2^e_c for the whole tile column
+      for (int c = tid; c < NC; c += T) {
+        const int em = expo[c];
+        pow2c[c] = __int_as_float((max(-126, min(127, em > 0 ? em - 1022 : 0)) + 127) << 23);
+      }
+      slice_stage(expo);
+    } else {
+      slice_stage(gexp);
+      __syncthreads();
+      // Y = X M' on the tensor cores: per 16 x 8 block the 28 digit pairs (p + q <= 6, weight
+      // d = p + q + 2 <= 8) accumulate exactly in FP32 per weight, then fold into double-float
+      float ymax[2] = {0.0f, 0.0f};
+#pragma unroll 1
+      for (int i = 0; i < 8; ++i) {
+        const int rb = rpart + WPC * i;
+        float ac[7][4];
 #pragma unroll
-      for (int k2 = 0; k2 < PAIRS; ++k2) {
-        const int pi = tid + T * k2, c = (2 * pi) / KT, r = (2 * pi) % KT;
-        Ar::Acc s0 = Ar::acc_zero(), s1 = Ar::acc_zero();
-        if (c < n) {
-          const int kend = XF == kXUpper ? c + 1 : n;
-          for (int kk = 0; kk < kend; ++kk) {
-            df w0, w1;
-            if constexpr (sizeof(S) == 8) {
-              w0 = stage_df[kk * KT + r];
-              w1 = stage_df[kk * KT + r + 1];
-            } else {
-              w0 = df{(float)stage[kk * KT + r], 0.0f};
-              w1 = df{(float)stage[kk * KT + r + 1], 0.0f};
-            }
-            const df mk = Mv[kk * NC + c];
-            Ar::acc_fma(s0, w0, mk);
-            Ar::acc_fma(s1, w1, mk);
+        for (int d = 0; d < 7; ++d)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) ac[d][e] = 0.0f;
+#pragma unroll
+        for (int ks = 0; ks < KSTEPS; ++ks) {
+          if (ks < ksw) {
+            unsigned af[7][4];
+            const int krow = 16 * ks + 8 * (lane >> 4) + (lane & 7);
+            const int rcol = 16 * rb + 8 * ((lane >> 3) & 1);
+#pragma unroll
+            for (int p = 0; p < 7; ++p)
+              ldsm_x4_t(af[p][0], af[p][1], af[p][2], af[p][3], slices + ((size_t)p * NC + krow) * LDR + rcol);
+#pragma unroll
+            for (int p = 0; p < 7; ++p)
+#pragma unroll
+              for (int q = 0; q + p < 7; ++q)
+                mma_bf16(ac[p + q], af[p][0], af[p][1], af[p][2], af[p][3], bq[ks][q][0], bq[ks][q][1]);
           }
         }
-        yv[2 * k2] = Ar::acc_get(s0);
-        yv[2 * k2 + 1] = Ar::acc_get(s1);
-        unsigned e0 = (__float_as_uint(yv[2 * k2].hi) >> 23) & 0xff;
-        unsigned e1 = (__float_as_uint(yv[2 * k2 + 1].hi) >> 23) & 0xff;
-        unsigned em = __reduce_max_sync(0xffffffffu, max(e0, e1));
-        if (lane == 0 && em > 0) atomicMax(&expo[c], (int)em);
-      }
-    }
-    __syncthreads();
-    // per-column scale 2^e_c, |y| < 2^e_c for the whole tile column
-    for (int c = tid; c < NC; c += T) {
-      const int em = expo[c];
-      int e = 0;
-      if (em > 0) e = (XF == kXNone) ? em - 1022 : em - 126;
-      e = max(-126, min(127, e));
-      pow2c[c] = __int_as_float((e + 127) << 23);
-    }
-    // slicing: seven signed base-128 digits per value, two rows per 32-bit store
 #pragma unroll
-    for (int k2 = 0; k2 < PAIRS; ++k2) {
-      const int pi = tid + T * k2, c = (2 * pi) / KT, r = (2 * pi) % KT;
-      const int em = expo[c];
-      unsigned long long N[2];
-      unsigned sg[2];
+        for (int e = 0; e < 4; ++e) {
+          const int h = e & 1;
+          float hi = ac[6][e] * ysc[h][6], lo = 0.0f;  // smallest weight first
+#pragma unroll
+          for (int d = 5; d >= 0; --d) {
+            float s, err;
+            two_sum(hi, ac[d][e] * ysc[h][d], s, err);
+            hi = s;
+            lo = __fadd_rn(lo, err);
+          }
+          const df y = df_make(hi, lo);
+          ymax[h] = fmaxf(ymax[h], fabsf(y.hi));
+          ydf[(cbw * 8 + 2 * t4 + h) * LDY + 16 * rb + g + 8 * (e >> 1)] = y;
+        }
+      }
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        if constexpr (XF == kXNone) {
-          if constexpr (sizeof(S) == 8) {
-            N[h] = fixed_of_double((double)stage[c * KT + r + h], em, sg[h]);
-          } else {
-            float x = (float)stage[c * KT + r + h];
-            sg[h] = __float_as_uint(x) & 0x80000000u;
-            N[h] = fixed_of_float(x, em - 896);
-          }
-        } else {
-          const df y = yv[2 * k2 + h];
+        float v = ymax[h];
+        v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, 4));
+        v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, 8));
+        v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, 16));
+        const int em = (__float_as_int(v) >> 23) & 0xff;
+        if (g == 0 && em > 0) atomicMax(&expo[cbw * 8 + 2 * t4 + h], em);
+      }
+      __syncthreads();
+      // per-column scale 2^e_c, |y| < 2^e_c for the whole tile column
+      for (int c = tid; c < NC; c += T) {
+        const int em = expo[c];
+        pow2c[c] = __int_as_float((max(-126, min(127, em > 0 ? em - 126 : 0)) + 127) << 23);
+      }
+      // slicing of Y: seven signed base-128 digits per value, two rows per 32-bit store
+#pragma unroll 4
+      for (int k2 = 0; k2 < PAIRS; ++k2) {
+        const int pi = tid + T * k2, c = (2 * pi) / KT, r = (2 * pi) % KT;
+        const int em = expo[c];
+        unsigned long long N[2];
+        unsigned sg[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const df y = ydf[c * LDY + r + h];
           sg[h] = __float_as_uint(y.hi) & 0x80000000u;
           unsigned long long nh = fixed_of_float(y.hi, em);
           unsigned long long nl = fixed_of_float(y.lo, em);
           bool same = ((__float_as_uint(y.lo) ^ __float_as_uint(y.hi)) & 0x80000000u) == 0u;
           N[h] = same ? nh + nl : (nh > nl ? nh - nl : 0ull);
         }
-      }
 #pragma unroll
-      for (int p = 0; p < Sh::ND; ++p) {
-        const int sh = 7 * (Sh::ND - 1 - p);
-        unsigned lo16 = bf16_digit((unsigned)(N[0] >> sh) & 127u, sg[0]);
-        unsigned hi16 = bf16_digit((unsigned)(N[1] >> sh) & 127u, sg[1]);
-        *reinterpret_cast<unsigned*>(slices + ((size_t)p * NC + c) * LDR + r) = lo16 | (hi16 << 16);
+        for (int p = 0; p < Sh::ND; ++p) {
+          const int sh = 7 * (Sh::ND - 1 - p);
+          unsigned lo16 = bf16_digit((unsigned)(N[0] >> sh) & 127u, sg[0]);
+          unsigned hi16 = bf16_digit((unsigned)(N[1] >> sh) & 127u, sg[1]);
+          *reinterpret_cast<unsigned*>(slices + ((size_t)p * NC + c) * LDR + r) = lo16 | (hi16 << 16);
+        }
       }
     }
     __syncthreads();
@@ -567,6 +657,10 @@ __global__ void __launch_bounds__(256, 1) gram_tc_kernel(GramArgs<S> a) {
     }
   }
   __syncthreads();
+  if constexpr (XF == kXNone) {  // column exponents of the whole matrix, for the second pass
+    for (int c = tid; c < n; c += T)
+      if (colmax[c] > 0) atomicMax(&a.w.flags[64 + c], colmax[c]);
+  }
   // combine the row parts of each C tile and store this CTA's partial Gram matrix
   df* red = reinterpret_cast<df*>(smem + Sm::kOffSlices);  // [unit][G][4][32]
 #pragma unroll

@@ -12,14 +12,24 @@
 // which stays below 2^24: every FP32 accumulator is an exact integer.  Products with the
 // same weight d = p + q (p + q <= 8, the terms above 2^-56 of the leading one) share one
 // accumulator; each is scaled by 2^(e_i + e_j - 7d) (exact) and added into a double-float
-// accumulator per C entry.  The second pass forms Y = X M (M = R1^{-1} or B1) tile by tile
-// in double-float on the FP32 pipes, then slices Y the same way.
+// accumulator per C entry.
 //
-// Warp layout (8 warps): the C tiles (16-row blocks x 8-column blocks) are grouped by row
-// block into units of up to 2 column blocks, and the row tile is split into KS parts, so
-// that every warp owns the same number of units.  Per 16-row k-step a unit loads the A
-// fragments of all 7 digits and the B fragments of all 7 digits once and issues the 28
-// digit-pair MMAs from registers (one shared-memory fragment load feeds up to 7 MMAs).
+// The second pass forms Y = X M (M = R1^{-1} or B1) on the tensor cores as well.  X is sliced
+// at the column scale e_k of the whole matrix (the first pass records it), so that
+//   X M = sum_{p,q} 2^(-7(p+q)) dX_p M'  with  M' = diag(2^e_k) M,
+// a scale that no longer depends on k.  M' is sliced once per CTA, column by column, into
+// bf16 digits that stay in registers as MMA B fragments for the whole launch; per 16 x 8
+// block of Y the 28 digit pairs again accumulate exactly in FP32 per weight, and the seven
+// weights are summed into one double-float per element.  Y is then sliced at its own
+// per-tile column scale and fed to the Gram products above.
+//
+// Warp layout of the Gram products (8 warps): the C tiles (16-row blocks x 8-column blocks)
+// are grouped by row block into units of up to 2 column blocks, and the row tile is split
+// into KS parts, so that every warp owns the same number of units.  Per 16-row k-step a
+// unit loads the A fragments of all 7 digits and the B fragments of all 7 digits once and
+// issues the 28 digit-pair MMAs from registers (one shared-memory fragment load feeds up to
+// 7 MMAs).  In the product Y = X M' a warp owns one 8-column block of Y and 8 of its 16-row
+// blocks.
 #pragma once
 
 #include "common.cuh"
@@ -48,19 +58,20 @@ struct TcShape {
 template <int NC, typename S>
 struct TcSmem {
   using Sh = TcShape<NC>;
+  static constexpr int LDY = Sh::KT + 4;                    // padded double-float row of Y
   static constexpr size_t kStage = sizeof(S) * NC * Sh::KT;
-  static constexpr size_t kStageDf = 8 * (size_t)NC * Sh::KT;  // in-place double-float view
-  static constexpr size_t kStageMax = kStage > kStageDf ? kStage : kStageDf;
+  static constexpr size_t kYdf = 8 * (size_t)NC * LDY;      // second pass: Y tile, same region
+  static constexpr size_t kStageMax = kStage > kYdf ? kStage : kYdf;
   static constexpr size_t kSlices = 2 * (size_t)Sh::ND * NC * Sh::LDR;
   static constexpr size_t kOffSlices = (kStageMax + 127) / 128 * 128;
-  static constexpr size_t kOffM = kOffSlices + kSlices;
-  static constexpr size_t kOffPow = kOffM + 8 * (size_t)NC * NC;   // float 2^e_c per column
+  static constexpr size_t kOffPow = kOffSlices + kSlices;          // float 2^e_c per column
   static constexpr size_t kOffExpo = kOffPow + 4 * NC;             // int max exponent per column
   static constexpr size_t kOffColmax = kOffExpo + 4 * NC;          // int, range check
-  static constexpr size_t kOffZero = (kOffColmax + 4 * NC + 15) / 16 * 16;
+  static constexpr size_t kOffGexp = kOffColmax + 4 * NC;          // int, column exponents of X
+  static constexpr size_t kOffZero = (kOffGexp + 4 * NC + 15) / 16 * 16;
   static constexpr size_t kOffMisc = kOffZero + 16;
   static constexpr size_t kMain = kOffMisc + 64 * 4;
-  static constexpr size_t kEpi = 8 * (4 * (size_t)NC * NC + 8 * NC) + 64 * 4 + 16;
+  static constexpr size_t kEpi = 8 * (4 * (size_t)NC * (NC + 1) + 8 * (NC + 1)) + 64 * 4 + 16;
   static constexpr size_t kBytes = kMain > kEpi ? kMain : kEpi;
 };
 
@@ -71,6 +82,12 @@ QL_DEV void ldsm_x4(unsigned& r0, unsigned& r1, unsigned& r2, unsigned& r3, cons
 }
 QL_DEV void ldsm_x2(unsigned& r0, unsigned& r1, const void* p) {
   asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n" : "=r"(r0), "=r"(r1) : "r"(smem_addr(p)));
+}
+// Four 8x8 b16 matrices, each stored with its rows as memory columns (ldmatrix .trans).
+QL_DEV void ldsm_x4_t(unsigned& r0, unsigned& r1, unsigned& r2, unsigned& r3, const void* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(smem_addr(p)));
 }
 QL_DEV void mma_bf16(float (&c)[4], unsigned a0, unsigned a1, unsigned a2, unsigned a3, unsigned b0, unsigned b1) {
   asm volatile(
