@@ -518,11 +518,14 @@ def run_serving(q, lib, torch, dev, count=20000, rate=2000.0, budget=60 << 30, m
     # alone-vs-mix check on a sample: the served R against a single TSQR call
     worst = 0.0
     bad = 0
+    codes = []
     cudart = lib
     for tk, r, b in tickets[:: max(1, len(tickets) // 24)]:
         s, res = srv.poll(tk)
         if s != 0 or res.status != 0:
             bad += 1
+            codes.append({"poll": int(s), "status": int(res.status), "m": r.m, "n": r.n, "kind": r.kind,
+                          "dtype": r.dtype, "kappa": r.kappa})
             continue
         n1 = r.n + 1 if r.kind == "lstsq" else r.n
         buf = np.zeros(n1 * n1)
@@ -547,7 +550,7 @@ def run_serving(q, lib, torch, dev, count=20000, rate=2000.0, budget=60 << 30, m
         "submitted": submitted, "completed": int(st.completed), "offered_s": round(t_sub, 2),
         "wall_s": round(t_all, 2), "solves_per_s": round(st.completed / max(t_all, 1e-9), 1),
         "p50_ms": round(st.p50_ms, 3), "p99_ms": round(st.p99_ms, 3), "mean_ms": round(st.mean_ms, 3),
-        "hbm_peak_gb": round(st.hbm_peak_bytes / 1e9, 2), "sample_status_errors": bad,
+        "hbm_peak_gb": round(st.hbm_peak_bytes / 1e9, 2), "sample_status_errors": bad, "sample_failures": codes,
         "max_err_over_tol_alone_vs_mix": round(worst, 4),
     }
 

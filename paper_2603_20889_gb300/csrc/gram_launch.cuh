@@ -9,6 +9,7 @@
 #include "internal.h"
 #include "small_dense.cuh"
 #include "gram_tc.cuh"
+#include "gram_umma.cuh"
 
 namespace ql {
 
@@ -40,6 +41,7 @@ struct GramArgs {
   double* resnorm;
   double* Rext;
   int32_t* info;
+  int bulk;  // every column starts 16-byte aligned: full tiles load with bulk copies
 };
 
 QL_DEV double qnan() { return __longlong_as_double(0x7ff8000000000000ll); }
@@ -704,7 +706,7 @@ ql_status gram_tc_launch_one(const GramCall& c, const GramWs& w, int pass) {
   int64_t g = (int64_t)device_sm_count() * occ;
   if (g > tiles) g = tiles;
   if (g < 1) g = 1;
-  GramArgs<S> a;
+  GramArgs<S> a{};
   a.src.A = static_cast<const S*>(c.A);
   a.src.lda = c.lda;
   a.src.b = static_cast<const S*>(c.b);
@@ -725,6 +727,465 @@ ql_status gram_tc_launch_one(const GramCall& c, const GramWs& w, int pass) {
   a.resnorm = c.resnorm;
   a.Rext = c.Rext;
   a.info = c.info;
+  count_launch();
+  kern<<<(int)g, Sh::T, Sm::kBytes, c.stream>>>(a);
+  return cudaPeekAtLastError() == cudaSuccess ? QL_OK : QL_ERR_CUDA;
+}
+
+// Tensor-core Gram pass on tcgen05 (double-float policy only): see gram_umma.cuh.  The
+// second pass forms Y = X M' with mma.sync as in gram_tc_kernel (B fragments of M' in
+// registers), reading X's digit planes in the core-matrix layout.
+template <int NC, typename S, int XF>
+__global__ void __launch_bounds__(256, 1) gram_umma_kernel(GramArgs<S> a) {
+  using Sh = UmmaShape<NC>;
+  using Sm = UmmaSmem<NC, S>;
+  constexpr int T = 256, KT = Sh::KT, LDS = Sm::LDS, LDY = Sm::LDY, SP = Sh::SP, PLANE = Sh::PLANE;
+  constexpr int SBO = Sh::SBO, LBO = Sh::LBO;
+  constexpr int PAIRS = NC * KT / 2 / T;        // row pairs (and core-matrix quarters) per thread and tile
+  constexpr int KSTEPS = NC / 16;               // 16-wide k-steps of Y = X M'
+  constexpr int WPC = 8 / (NC / 8);             // warps per 8-column block of Y
+  constexpr int HALF = NC / 2;                  // accumulator columns per thread
+  constexpr int CPG = KT / 8;                   // core matrices per 8-column group
+  constexpr uint32_t IDESC = umma_idesc_bf16(128, NC);
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int tid = threadIdx.x, n = a.n, lane = tid & 31, warp = tid >> 5;
+
+  if (a.pass == 2 && *(volatile int*)&a.w.flags[0] != 0) return;  // the FP64 launches redo it
+  if (a.pass == 2 && *(volatile int*)&a.w.flags[1] != 0) {         // first pass broke down
+    if (blockIdx.x == 0) write_nan_outputs(a, T);
+    return;
+  }
+  unsigned char* digits = smem;  // 7 planes, core-matrix layout
+  S* stage = reinterpret_cast<S*>(smem + Sm::kOffStage);
+  df* ydf = reinterpret_cast<df*>(smem + Sm::kOffStage);  // second pass: Y, column c at c * LDY
+  float* pow2c = reinterpret_cast<float*>(smem + Sm::kOffPow);
+  int* expo = reinterpret_cast<int*>(smem + Sm::kOffExpo);
+  int* colmax = reinterpret_cast<int*>(smem + Sm::kOffColmax);
+  int* gexp = reinterpret_cast<int*>(smem + Sm::kOffGexp);
+  int* misc = reinterpret_cast<int*>(smem + Sm::kOffMisc);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + Sm::kOffBar);
+  uint64_t* lbar = reinterpret_cast<uint64_t*>(smem + Sm::kOffBar + 8);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + Sm::kOffBar + 16);
+
+  for (int i = tid; i < NC; i += T) {
+    colmax[i] = 0;
+    gexp[i] = (XF != kXNone && i < n) ? __ldcg(&a.w.flags[64 + i]) : 0;
+  }
+  __syncthreads();
+  const int g = lane >> 2, t4 = lane & 3;
+
+  // ---- second pass: this warp's 8-column block of Y and the B fragments of M' = diag(2^e_k) M
+  const int cbw = (NC == 64 && warp >= 4) ? 11 - warp : warp / WPC;
+  const int rpart = (NC == 64) ? 0 : warp % WPC;
+  const int ksw = XF == kXUpper ? (cbw >> 1) + 1 : KSTEPS;
+  unsigned bq[XF != kXNone ? KSTEPS : 1][7][2];
+  float ysc[2][7];  // 2^(f_j - 7(d + 2)) for this thread's two Y columns and the 7 weights
+  if constexpr (XF != kXNone) {
+    const double* M = a.w.keep + (size_t)n * n;  // pass-1 output, row-major, ld n
+    const int jb = cbw * 8 + g;
+    double mv[KSTEPS][4];
+    int F = 0;
+#pragma unroll
+    for (int ks = 0; ks < KSTEPS; ++ks)
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        const int k = 16 * ks + 2 * t4 + (h & 1) + 8 * (h >> 1);
+        double v = 0.0;
+        if (k < n && jb < n && (XF != kXUpper || k <= jb)) {
+          const int ek = gexp[k];
+          if (ek > 0) v = __ldcg(M + (size_t)k * n + jb) * __longlong_as_double((long long)(ek + 1) << 52);
+        }
+        mv[ks][h] = v;
+        F = max(F, (int)((__double_as_longlong(v) >> 52) & 0x7ff));
+      }
+    F = max(F, __shfl_xor_sync(0xffffffffu, F, 1));
+    F = max(F, __shfl_xor_sync(0xffffffffu, F, 2));  // max over column jb of M'
+#pragma unroll
+    for (int ks = 0; ks < KSTEPS; ++ks) {
+      unsigned long long N[4];
+      unsigned sg[4];
+#pragma unroll
+      for (int h = 0; h < 4; ++h) N[h] = fixed_of_double(mv[ks][h], F, sg[h]);
+#pragma unroll
+      for (int q = 0; q < 7; ++q) {
+        const int sh = 7 * (6 - q);
+        bq[ks][q][0] = bf16_digit((unsigned)(N[0] >> sh) & 127u, sg[0]) |
+                       (bf16_digit((unsigned)(N[1] >> sh) & 127u, sg[1]) << 16);
+        bq[ks][q][1] = bf16_digit((unsigned)(N[2] >> sh) & 127u, sg[2]) |
+                       (bf16_digit((unsigned)(N[3] >> sh) & 127u, sg[3]) << 16);
+      }
+    }
+    bool bad = false;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int Fj = __shfl_sync(0xffffffffu, F, 4 * (2 * t4 + h));
+      const int f = Fj - 1022;  // |M'(:, j)| < 2^f
+      if (Fj > 0 && (f < -70 || f > 100)) bad = true;
+#pragma unroll
+      for (int d = 0; d < 7; ++d) {
+        const int e = f - 7 * (d + 2);
+        ysc[h][d] = (Fj > 0 && !bad) ? __int_as_float((e + 127) << 23) : 0.0f;
+      }
+    }
+    if (__syncthreads_or(bad)) {  // out of the double-float range: the FP64 launches redo it
+      if (tid == 0) atomicOr(&a.w.flags[0], 1);
+      gram_finish<NC, T, S, ArithDF>(a, smem, colmax, misc);
+      return;
+    }
+  }
+
+  // ---- tensor memory for the 7 accumulator blocks, and the MMA-completion barrier
+  if (warp == 0) tmem_alloc(tslot, Sh::TCOLS);
+  if (tid == 0) {
+    mbar_init(mbar, 1);
+    mbar_init(lbar, 1);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = *tslot;
+
+  const int qd = warp & 3, hh = warp >> 2;  // TMEM lane quarter and column half of this warp
+  const int L = 32 * qd + lane, kq = L / NC, li = L % NC;
+  df acc[HALF];
+#pragma unroll
+  for (int j = 0; j < HALF; ++j) acc[j] = df{0.0f, 0.0f};
+
+  const int k = gridDim.x, bid = blockIdx.x;
+  const int64_t t0 = a.tiles * bid / k, t1 = a.tiles * (bid + 1) / k;
+  // a full tile of 16-byte aligned columns arrives by bulk copies (one per column, issued by
+  // one thread, completion on lbar); otherwise element by element with zero fill
+  auto tile_bulk = [&](int64_t t) { return a.bulk != 0 && (t + 1) * KT <= a.m; };
+  auto issue = [&](int64_t t) {
+    const int64_t row0 = t * KT;
+    if (tile_bulk(t)) {
+      if (tid == 32) {  // warp 1: warp 0 issues the MMAs meanwhile
+        mbar_arrive_expect_tx(lbar, (uint32_t)(n * KT * sizeof(S)));
+        for (int c = 0; c < n; ++c) bulk_g2s(stage + c * LDS, a.src.col(c) + row0, KT * sizeof(S), lbar);
+      }
+      return;
+    }
+#pragma unroll 1
+    for (int c = 0; c < NC; ++c) {
+      const S* col = a.src.col(c < n ? c : 0);
+      for (int r = tid; r < KT; r += T) {
+        int64_t row = row0 + r;
+        bool v = c < n && row < a.m;
+        cp_async_elem<S>(stage + c * LDS + r, v ? col + row : col, v);
+      }
+    }
+    cp_async_commit();
+  };
+  uint32_t lphase = 0;
+  auto wait_tile = [&](int64_t t) -> bool {  // this thread's view: the staged tile t has landed
+    if (!tile_bulk(t)) {
+      cp_async_wait_all();
+      return true;
+    }
+    const bool landed = mbar_wait_bounded(lbar, lphase);
+    lphase ^= 1u;
+    return landed;
+  };
+  // seven signed base-128 digits per value into the core-matrix layout: a warp writes one
+  // 8 x 8 core matrix (128 contiguous bytes) per step, a lane two rows of one column
+  auto put_digits = [&](int c, int r, unsigned long long N0, unsigned s0, unsigned long long N1, unsigned s1) {
+    unsigned char* base = digits + (c >> 3) * SBO + (r >> 3) * LBO + (c & 7) * 16 + (r & 7) * 2;
+    const unsigned sgn = (s0 >> 16) | s1;  // the sign bits of both bf16 halves
+#pragma unroll
+    for (int p = 0; p < Sh::ND; ++p) {
+      const int sh = 7 * (Sh::ND - 1 - p);
+      // d -> float exactly as (2^23 + d) - 2^23; the upper halves of the two floats are the
+      // bf16 digits, packed with one byte permute
+      const float f0 = __fsub_rn(__uint_as_float(0x4B000000u | ((unsigned)(N0 >> sh) & 127u)), 8388608.0f);
+      const float f1 = __fsub_rn(__uint_as_float(0x4B000000u | ((unsigned)(N1 >> sh) & 127u)), 8388608.0f);
+      *reinterpret_cast<unsigned*>(base + p * PLANE) = __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632) | sgn;
+    }
+  };
+  // the staged X, ex[c] the biased double exponent that bounds column c
+  auto slice_stage = [&](const int* ex) {
+#pragma unroll 4
+    for (int k2 = 0; k2 < PAIRS; ++k2) {
+      const int cm = warp + 8 * k2, c = 8 * (cm / CPG) + (lane >> 2), r = 8 * (cm % CPG) + 2 * (lane & 3);
+      const int em = c < n ? ex[c] : 0;  // columns past n are zero (a bulk-loaded stage holds stale data there)
+      unsigned long long N[2];
+      unsigned sg[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        if constexpr (sizeof(S) == 8) {
+          const double x = em > 0 ? (double)stage[c * LDS + r + h] : 0.0;
+          N[h] = fixed_of_double(x, em, sg[h]);
+        } else {
+          float x = em > 0 ? (float)stage[c * LDS + r + h] : 0.0f;
+          sg[h] = __float_as_uint(x) & 0x80000000u;
+          N[h] = em > 0 ? fixed_of_float(x, em - 896) : 0ull;
+        }
+      }
+      put_digits(c, r, N[0], sg[0], N[1], sg[1]);
+    }
+  };
+
+  bool ok = true;
+  if (t0 < t1) issue(t0);
+  __syncthreads();
+  uint32_t phase = 0;
+  for (int64_t t = t0; t < t1; ++t) {
+    if (!__syncthreads_and(wait_tile(t))) {  // the copy engine did not deliver: FP64 redoes the call
+      ok = false;
+      break;
+    }
+    for (int i = tid; i < NC; i += T) expo[i] = 0;
+    __syncthreads();
+    if constexpr (XF == kXNone) {
+      // column maxima of the biased double exponent (and the range record)
+#pragma unroll 4
+      for (int k2 = 0; k2 < PAIRS; ++k2) {
+        const int pi = tid + T * k2, c = (2 * pi) / KT, r = (2 * pi) % KT;
+        unsigned em = 0;
+        if (c < n) {  // warp-uniform: a warp covers 64 rows of one column
+          if constexpr (sizeof(S) == 8) {
+            unsigned long long b0 = (unsigned long long)__double_as_longlong((double)stage[c * LDS + r]);
+            unsigned long long b1 = (unsigned long long)__double_as_longlong((double)stage[c * LDS + r + 1]);
+            em = max((unsigned)((b0 >> 52) & 0x7ff), (unsigned)((b1 >> 52) & 0x7ff));
+          } else {
+            unsigned e0 = (__float_as_uint((float)stage[c * LDS + r]) >> 23) & 0xff;
+            unsigned e1 = (__float_as_uint((float)stage[c * LDS + r + 1]) >> 23) & 0xff;
+            em = max(e0 ? e0 + 896 : 0u, e1 ? e1 + 896 : 0u);
+          }
+        }
+        em = __reduce_max_sync(0xffffffffu, em);
+        if (lane == 0 && em > 0) {
+          atomicMax(&expo[c], (int)em);
+          atomicMax(&colmax[c], (int)em);
+        }
+      }
+      __syncthreads();
+      for (int c = tid; c < NC; c += T) {
+        const int em = expo[c];
+        pow2c[c] = __int_as_float((max(-126, min(127, em > 0 ? em - 1022 : 0)) + 127) << 23);
+      }
+      slice_stage(expo);
+    } else {
+      slice_stage(gexp);
+      __syncthreads();
+      // Y = X M' (mma.sync): per 16 x 8 block the 28 digit pairs accumulate exactly in FP32
+      // per weight, then fold into double-float
+      float ymax[2] = {0.0f, 0.0f};
+#pragma unroll 1
+      for (int i = 0; i < 8; ++i) {
+        const int rb = rpart + WPC * i;
+        float ac[7][4];
+#pragma unroll
+        for (int d = 0; d < 7; ++d)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) ac[d][e] = 0.0f;
+#pragma unroll
+        for (int ks = 0; ks < KSTEPS; ++ks) {
+          if (ks < ksw) {
+            unsigned af[7][4];
+            // ldmatrix .trans of core matrix (column group 2 ks + K, row group 2 rb + R), row lane & 7
+            const unsigned char* ap = digits + (2 * ks + (lane >> 4)) * SBO + (2 * rb + ((lane >> 3) & 1)) * LBO +
+                                      (lane & 7) * 16;
+#pragma unroll
+            for (int p = 0; p < 7; ++p) ldsm_x4_t(af[p][0], af[p][1], af[p][2], af[p][3], ap + p * PLANE);
+#pragma unroll
+            for (int p = 0; p < 7; ++p)
+#pragma unroll
+              for (int q = 0; q + p < 7; ++q)
+                mma_bf16(ac[p + q], af[p][0], af[p][1], af[p][2], af[p][3], bq[ks][q][0], bq[ks][q][1]);
+          }
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int h = e & 1;
+          float hi = ac[6][e] * ysc[h][6], lo = 0.0f;  // smallest weight first
+#pragma unroll
+          for (int d = 5; d >= 0; --d) {
+            float s, err;
+            two_sum(hi, ac[d][e] * ysc[h][d], s, err);
+            hi = s;
+            lo = __fadd_rn(lo, err);
+          }
+          const df y = df_make(hi, lo);
+          ymax[h] = fmaxf(ymax[h], fabsf(y.hi));
+          ydf[(cbw * 8 + 2 * t4 + h) * LDY + 16 * rb + g + 8 * (e >> 1)] = y;
+        }
+      }
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        float v = ymax[h];
+        v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, 4));
+        v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, 8));
+        v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, 16));
+        const int em = (__float_as_int(v) >> 23) & 0xff;
+        if (g == 0 && em > 0) atomicMax(&expo[cbw * 8 + 2 * t4 + h], em);
+      }
+      __syncthreads();
+      for (int c = tid; c < NC; c += T) {
+        const int em = expo[c];
+        pow2c[c] = __int_as_float((max(-126, min(127, em > 0 ? em - 126 : 0)) + 127) << 23);
+      }
+      // slicing of Y at its per-tile column scale
+#pragma unroll 4
+      for (int k2 = 0; k2 < PAIRS; ++k2) {
+        const int cm = warp + 8 * k2, c = 8 * (cm / CPG) + (lane >> 2), r = 8 * (cm % CPG) + 2 * (lane & 3);
+        const int em = expo[c];
+        unsigned long long N[2];
+        unsigned sg[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const df y = ydf[c * LDY + r + h];
+          sg[h] = __float_as_uint(y.hi) & 0x80000000u;
+          unsigned long long nh = fixed_of_float(y.hi, em);
+          unsigned long long nl = fixed_of_float(y.lo, em);
+          bool same = ((__float_as_uint(y.lo) ^ __float_as_uint(y.hi)) & 0x80000000u) == 0u;
+          N[h] = same ? nh + nl : (nh > nl ? nh - nl : 0ull);
+        }
+        put_digits(c, r, N[0], sg[0], N[1], sg[1]);
+      }
+    }
+    fence_proxy_async_smem();  // the digit planes are read by the tensor core
+    __syncthreads();
+    if (t + 1 < t1) issue(t + 1);
+    // 7 accumulator blocks: block tb = p0 + q collects planes p0.. (stacked) times plane q
+    if (tid == 0) {
+      tc_fence_after();
+      // descriptor of plane 0, k-step 0; other planes and k-steps add (byte offset >> 4) to
+      // the 14-bit address field, which stays below 2^14 (shared addresses < 256 KB)
+      const uint64_t d0 = umma_sdesc(smem_addr(digits), LBO, SBO);
+#pragma unroll 1
+      for (int kk = 0; kk < KT / 16; ++kk) {
+        const uint64_t dk = d0 + (uint64_t)((kk * 2 * LBO) >> 4);
+#pragma unroll
+        for (int p0 = 0; p0 < 7; p0 += SP)
+#pragma unroll
+          for (int q = 0; q + p0 < 7; ++q)
+            umma_bf16(tbase + (uint32_t)((p0 + q) * NC), dk + (uint64_t)((p0 * PLANE) >> 4),
+                      dk + (uint64_t)((q * PLANE) >> 4), IDESC, (kk > 0 || p0 > 0) ? 1u : 0u);
+      }
+      umma_commit(mbar);
+    }
+    const bool done = mbar_wait_bounded(mbar, phase);
+    phase ^= 1u;
+    if (!__syncthreads_and(done)) {  // the tensor core did not finish: let FP64 redo the call
+      if (t + 1 < t1) wait_tile(t + 1);  // no copy may still be writing when the CTA moves on
+      ok = false;
+      break;
+    }
+    tc_fence_after();
+    // fold the blocks into the double-float accumulators: lane L holds plane offset kq and
+    // column li, so block tb carries weight w = tb + kq (0-based; weights above 6 are beyond
+    // the truncation).  Per column the seven weights are summed first: blocks 3..6 in FP32
+    // (together below 2^-21 of the leading weight), blocks 2, 1, 0 with exact two-sums; the
+    // result enters the accumulator with one double-float add.
+    {
+      const float fi = pow2c[li];
+      float sw[7];
+      uint32_t vm[7];  // lanes beyond the truncation may hold non-finite products of "plane 7": masked, not scaled
+#pragma unroll
+      for (int tb = 0; tb < 7; ++tb) {
+        sw[tb] = tb + kq <= 6 ? fi * __int_as_float((127 - 7 * (tb + kq + 2)) << 23) : 0.0f;
+        vm[tb] = tb + kq <= 6 ? 0xffffffffu : 0u;
+      }
+      const uint32_t lane_base = tbase + ((uint32_t)(32 * qd) << 16) + (uint32_t)(hh * HALF);
+#pragma unroll
+      for (int c0 = 0; c0 < HALF; c0 += 4) {
+        uint32_t v[7][4];
+#pragma unroll
+        for (int tb = 0; tb < 7; ++tb) tmem_ld(lane_base + (uint32_t)(tb * NC + c0), v[tb]);
+        tmem_ld_wait();
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          float hi = __uint_as_float(v[6][j] & vm[6]) * sw[6];
+          hi = __fmaf_rn(__uint_as_float(v[5][j] & vm[5]), sw[5], hi);
+          hi = __fmaf_rn(__uint_as_float(v[4][j] & vm[4]), sw[4], hi);
+          hi = __fmaf_rn(__uint_as_float(v[3][j] & vm[3]), sw[3], hi);
+          float lo = 0.0f;
+#pragma unroll
+          for (int tb = 2; tb >= 0; --tb) {
+            float s2, e2;
+            two_sum(hi, __uint_as_float(v[tb][j] & vm[tb]) * sw[tb], s2, e2);
+            hi = s2;
+            lo = __fadd_rn(lo, e2);
+          }
+          const float fj = pow2c[hh * HALF + c0 + j];
+          acc[c0 + j] = df_add(acc[c0 + j], df{hi * fj, lo * fj});
+        }
+      }
+    }
+    tc_fence_before();
+  }
+  cp_async_wait_all();  // an early exit may leave a prefetch in flight
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tbase, Sh::TCOLS);
+  if (!ok && tid == 0) atomicOr(&a.w.flags[0], 2);
+  if constexpr (XF == kXNone) {  // column exponents of the whole matrix, for the second pass
+    for (int c = tid; c < n; c += T)
+      if (colmax[c] > 0) atomicMax(&a.w.flags[64 + c], colmax[c]);
+  }
+  // combine the plane offsets of each entry and store this CTA's partial Gram matrix
+  df* red = reinterpret_cast<df*>(smem + Sm::kOffStage);  // [lane L][column]
+#pragma unroll
+  for (int j = 0; j < HALF; ++j) red[L * NC + hh * HALF + j] = acc[j];
+  __syncthreads();
+  double* part = a.w.partials + (size_t)bid * NC * NC;
+  for (int e = tid; e < NC * NC; e += T) {
+    const int i = e / NC, j = e % NC;
+    df s = df{0.0f, 0.0f};
+#pragma unroll
+    for (int kk = 0; kk < SP; ++kk) s = df_add(s, red[(kk * NC + i) * NC + j]);
+    __stcg(part + e, df_to_double(s));
+  }
+  gram_finish<NC, T, S, ArithDF>(a, smem, colmax, misc);
+}
+
+template <int NC, typename S, int XF>
+ql_status gram_umma_launch_one(const GramCall& c, const GramWs& w, int pass) {
+  using Sh = UmmaShape<NC>;
+  using Sm = UmmaSmem<NC, S>;
+  auto kern = gram_umma_kernel<NC, S, XF>;
+  static bool ready = false;
+  static std::mutex mu;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (!ready) {
+      if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sm::kBytes) != cudaSuccess)
+        return QL_ERR_CUDA;
+      ready = true;
+    }
+  }
+  // one CTA per SM: the shared memory allows no second one, and tensor memory is sized so
+  const int64_t tiles = (c.m + Sh::KT - 1) / Sh::KT;
+  int64_t g = (int64_t)device_sm_count();
+  if (g > tiles) g = tiles;
+  if (g < 1) g = 1;
+  GramArgs<S> a{};
+  a.src.A = static_cast<const S*>(c.A);
+  a.src.lda = c.lda;
+  a.src.b = static_cast<const S*>(c.b);
+  a.src.nA = c.nA;
+  a.m = c.m;
+  a.n = c.n;
+  a.tiles = tiles;
+  a.pass = pass;
+  a.method = c.method;
+  a.gated = 0;
+  a.epilogue = c.epilogue;
+  a.w = w;
+  a.R = c.R;
+  a.ldr = c.ldr;
+  a.Z = c.Z;
+  a.rank_tol = c.rank_tol;
+  a.x = c.x;
+  a.resnorm = c.resnorm;
+  a.Rext = c.Rext;
+  a.info = c.info;
+  {
+    auto aligned = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+    bool b = aligned(c.A) && ((size_t)c.lda * sizeof(S)) % 16 == 0;
+    if (c.nA < c.n) b = b && aligned(c.b);
+    a.bulk = b ? 1 : 0;
+  }
   count_launch();
   kern<<<(int)g, Sh::T, Sm::kBytes, c.stream>>>(a);
   return cudaPeekAtLastError() == cudaSuccess ? QL_OK : QL_ERR_CUDA;
@@ -752,7 +1213,7 @@ ql_status gram_launch_one(const GramCall& c, const GramWs& w, int pass, int gate
   int64_t g = (int64_t)device_sm_count() * occ;
   if (g > tiles) g = tiles;
   if (g < 1) g = 1;
-  GramArgs<S> a;
+  GramArgs<S> a{};
   a.src.A = static_cast<const S*>(c.A);
   a.src.lda = c.lda;
   a.src.b = static_cast<const S*>(c.b);
@@ -785,6 +1246,14 @@ ql_status gram_dispatch(const GramCall& c, const GramWs& w, int gated) {
     constexpr int NC = decltype(nc_tag)::value;
     if constexpr (NC >= 16 && std::is_same<Ar, ArithDF>::value) {
       if (tc_gram_enabled()) {
+        // tcgen05 for 64 columns; below that, stacking 128 / NC planes spreads every weight
+        // over 4 or 8 lane groups and the TMEM read-out costs more than mma.sync saves
+        if (NC == 64 && umma_gram_enabled()) {
+          ql_status st = gram_umma_launch_one<NC, S, kXNone>(c, w, 1);
+          if (st) return st;
+          if (c.method == QL_CHOLQR2) return gram_umma_launch_one<NC, S, kXUpper>(c, w, 2);
+          return gram_umma_launch_one<NC, S, kXFull>(c, w, 2);
+        }
         ql_status st = gram_tc_launch_one<NC, S, kXNone>(c, w, 1);
         if (st) return st;
         if (c.method == QL_CHOLQR2) return gram_tc_launch_one<NC, S, kXUpper>(c, w, 2);

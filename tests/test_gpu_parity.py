@@ -199,10 +199,11 @@ def test_cholqr2_breakdown_reports_pivot():
 
 @pytest.mark.parametrize("method", ["tsqr", "cholqr2"])
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
-def test_lstsq_matches_oracle(method, dtype):
+@pytest.mark.parametrize("m", [60013, 60000])  # unaligned columns; 16-byte aligned columns (bulk tile copies)
+def test_lstsq_matches_oracle(method, dtype, m):
     import paper_2603_20889_gb300 as q
 
-    A, b, _ = synth.lstsq_case(60013, 31, 1e3, seed=3)
+    A, b, _ = synth.lstsq_case(m, 31, 1e3, seed=3)
     if dtype == "f32":
         A, b = A.astype(np.float32), b.astype(np.float32)
     x_ref, rho_ref, Re_ref, info_ref = oracle.lstsq(A.astype(np.float64), b.astype(np.float64))
