@@ -37,6 +37,22 @@ LS_M, LS_N = 1 << 24, 31  # least-squares [A b] workload
 KAPPA = 1e4
 METHODS = ["tsqr", "cholqr2", "svqb2"]
 PASSES = {"tsqr": 1, "cholqr2": 2, "svqb2": 2}
+# DRAM bytes (read + write) per row of X per launch, from one ncu capture of the same kernel
+# on a smaller m (dram__bytes_read.sum + dram__bytes_write.sum of that launch / its m); the
+# roofline's "traffic" is this times m for the dominant call, null where no capture of the
+# current kernel exists.
+MEASURED_TRAFFIC_PER_ROW = {
+    ("tsqr", 64): (1.075439e9 + 3.721472e6) / 2 ** 21,     # tsqr_kernel<64>, m = 2^21
+    ("tsqr", 8): (1.073880e9 + 3.648512e6) / 2 ** 24,      # tsqr_kernel<8>, m = 2^24
+    ("cholqr2", 64): (2.148391e9 + 3.803648e6) / 2 ** 22,  # gram_umma_kernel<64> first pass, m = 2^22
+    ("svqb2", 32): (1.074148e9 + 3.180544e6) / 2 ** 22,    # gram_tc_kernel<32> first pass, m = 2^22
+}
+
+
+def kernel_name(meth: str, n: int) -> str:
+    if meth == "tsqr":
+        return "tsqr_kernel"
+    return "gram_umma_kernel" if n > 32 else ("gram_tc_kernel" if n > 8 else "gram_kernel")
 METRIC = "Q-less QR effective GB/s (8mn B/time)"
 WORKLOAD = ("Q-less QR condition sweep: X = G S, m = 2^25 rows, n in {1,2,4,8,16,32,64}, kappa = 1e4, "
             "FP64 storage; TSQR + Cholesky-QR2 + SVQB2 per n; plus least squares via the QR of [A b], "
@@ -271,9 +287,11 @@ def run_ours(args, rank, world, local_rank):
     # the timed share of the dominant kernel: one pass = one launch reading its bytes
     kern_ms = dms / PASSES.get(dmeth, 1)
     achieved = nbytes(dmeth, dn) / kern_ms / 1e6
+    per_row = MEASURED_TRAFFIC_PER_ROW.get((dmeth, dn))
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": None, "peak_source": peak_kind,
-                "kernel": f"{'tsqr_kernel' if dmeth == 'tsqr' else 'gram_kernel'} ({dmeth}, n={dn}, m=2^25)",
+                "frac": round(achieved / peak, 4), "traffic": int(per_row * M) if per_row else None,
+                "peak_source": peak_kind,
+                "kernel": f"{kernel_name(dmeth, dn)} ({dmeth}, n={dn}, m=2^25)",
                 "algorithmic_bytes_per_launch": int(nbytes(dmeth, dn)),
                 "note": "per-launch time from CUDA events around the call on its stream; Gram methods: "
                         "call time / 2 passes"}
@@ -340,6 +358,16 @@ def run_e2e(args, q, lib, torch, dev, Xs, ws, wsb, stream, ls):
                                                      v[1].element_size() for v in hls.values())
     d2h = sum(Rh[n].numel() * 8 * len(METHODS) for n in NS) + len(hls) * (LS_N + 1) * 8
     seq = [0]
+    ls_copied = {k: _t.cuda.Event() for k in hls}
+    ls_used = {k: _t.cuda.Event() for k in hls}
+
+    def h2d(dst, src):
+        """Host -> device in 1 GB pieces on the current stream: single pinned copies of
+        several GB ran at well under half the link rate on this machine."""
+        d, h = dst.view(-1), src.reshape(-1)
+        ch = (1 << 30) // h.element_size()
+        for i in range(0, h.numel(), ch):
+            d[i:i + ch].copy_(h[i:i + ch], non_blocking=True)
 
     def step():
         for n in NS:
@@ -348,7 +376,7 @@ def run_e2e(args, q, lib, torch, dev, Xs, ws, wsb, stream, ls):
             dst = bufs[b][: host[n].numel()]
             cstream.wait_event(used[b])
             with _t.cuda.stream(cstream):
-                dst.copy_(host[n].view(-1), non_blocking=True)
+                h2d(dst, host[n])
                 copied[b].record(cstream)
             stream.wait_event(copied[b])
             X = dst.data_ptr()
@@ -364,10 +392,16 @@ def run_e2e(args, q, lib, torch, dev, Xs, ws, wsb, stream, ls):
                 Rh[n].copy_(Rd[n], non_blocking=True)
             used[b].record(stream)
         for name, (Ah, bh, Ad, bd, dt) in hls.items():  # least squares: [A b] from host, x back
-            Ad.copy_(Ah, non_blocking=True)
-            bd.copy_(bh, non_blocking=True)
+            cstream.wait_event(ls_used[name])
+            with _t.cuda.stream(cstream):  # queued behind the sweep's copies: overlaps its last factorisations
+                h2d(Ad, Ah)
+                h2d(bd, bh)
+                ls_copied[name].record(cstream)
+        for name, (Ah, bh, Ad, bd, dt) in hls.items():
+            stream.wait_event(ls_copied[name])
             lib.ql_lstsq_qless(LS_M, LS_N, Ad.data_ptr(), LS_M, bd.data_ptr(), dt, q.QL_TSQR, xd.data_ptr(),
                                xd[LS_N:].data_ptr(), None, inf.data_ptr(), ws.data_ptr(), wsb, sptr)
+            ls_used[name].record(stream)
             xh.copy_(xd, non_blocking=True)
 
     step()
@@ -385,8 +419,9 @@ def run_e2e(args, q, lib, torch, dev, Xs, ws, wsb, stream, ls):
     del host, bufs, hls
     return {"value": round(bytes_step / (ms / 1e3) / 1e9, 2), "unit": "GB/s", "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h), "ms_per_step": round(ms, 3),
-            "note": "each X copied host->device once per step from pinned memory on a second stream "
-                    "(double-buffered, overlapping the previous matrix's factorisations); every R read back"}
+            "note": "each X (and each [A b]) copied host->device once per step from pinned memory in 1 GB "
+                    "pieces on a second stream (double-buffered, overlapping the previous matrix's "
+                    "factorisations); every R and x read back"}
 
 
 # ------------------------------------------------------------------ batched and serving forms
