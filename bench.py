@@ -361,7 +361,7 @@ def run_e2e(args, q, lib, torch, dev, Xs, ws, wsb, stream, ls):
     ls_copied = {k: _t.cuda.Event() for k in hls}
     ls_used = {k: _t.cuda.Event() for k in hls}
 
-    def h2d(dst, src):
+    def copy_in(dst, src):
         """Host -> device in 1 GB pieces on the current stream: single pinned copies of
         several GB ran at well under half the link rate on this machine."""
         d, h = dst.view(-1), src.reshape(-1)
@@ -376,7 +376,7 @@ def run_e2e(args, q, lib, torch, dev, Xs, ws, wsb, stream, ls):
             dst = bufs[b][: host[n].numel()]
             cstream.wait_event(used[b])
             with _t.cuda.stream(cstream):
-                h2d(dst, host[n])
+                copy_in(dst, host[n])
                 copied[b].record(cstream)
             stream.wait_event(copied[b])
             X = dst.data_ptr()
@@ -394,8 +394,8 @@ def run_e2e(args, q, lib, torch, dev, Xs, ws, wsb, stream, ls):
         for name, (Ah, bh, Ad, bd, dt) in hls.items():  # least squares: [A b] from host, x back
             cstream.wait_event(ls_used[name])
             with _t.cuda.stream(cstream):  # queued behind the sweep's copies: overlaps its last factorisations
-                h2d(Ad, Ah)
-                h2d(bd, bh)
+                copy_in(Ad, Ah)
+                copy_in(bd, bh)
                 ls_copied[name].record(cstream)
         for name, (Ah, bh, Ad, bd, dt) in hls.items():
             stream.wait_event(ls_copied[name])
@@ -527,6 +527,8 @@ def run_serving(q, lib, torch, dev, count=20000, rate=2000.0, budget=60 << 30, m
     M = 1 << 22
     pools64 = [synth.conditioned_device(M, 65, k, seed=77 + i, device=dev) for i, k in enumerate(kb)]
     pools32 = [p.float() for p in pools64]
+    # the server's streams do not wait on the default stream: the pools must be complete
+    torch.cuda.synchronize()
     srv = q.Server(budget, 8192, 4)
     t0 = time.perf_counter()
     tickets = []

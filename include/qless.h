@@ -231,6 +231,10 @@ typedef struct {
  * the budget covers the server's workspaces and outputs) and `max_slots` allow, launches
  * each admitted group as one batched persistent kernel on one of `streams` CUDA streams,
  * so groups overlap on the device, and completes them as their events fire.
+ *
+ * The server's streams are non-blocking and wait on nothing of the caller's: a request's
+ * X and b must be complete in device memory when it is submitted (synchronise the stream
+ * that produced them first), and must stay unchanged until the request completes.
  */
 ql_server* ql_server_create(size_t hbm_budget_bytes, int32_t max_slots, int32_t streams);
 ql_status ql_server_submit(ql_server* s, const ql_request* req, uint64_t* ticket);

@@ -206,6 +206,7 @@ def test_server_completes_when_the_budget_is_the_limit():
 
     m, n = 1 << 18, 10  # 21 MB per request
     X = torch.randn((n, m), dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()  # the server's streams do not wait on the default stream
     srv = q.Server(128 << 20, 4096, 2)  # room for ~4 requests' data at a time
     tickets = [srv.submit(q.Request(m=m, n=n, ld=m, X=X.data_ptr(), dtype=q.QL_F64, kind=0, b=None,
                                     kappa_hint=1.0)) for _ in range(40)]
