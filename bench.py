@@ -49,6 +49,11 @@ MEASURED_TRAFFIC_PER_ROW = {
 }
 
 
+# FP32 instructions of one double-float (dot, update) pair of the Householder column step:
+# an accumulating product (12) and a product subtracted with renormalisation (15)
+DF_INSTR_PER_PAIR = 27
+
+
 def kernel_name(meth: str, n: int) -> str:
     if meth == "tsqr":
         return "tsqr_kernel"
@@ -288,13 +293,31 @@ def run_ours(args, rank, world, local_rank):
     kern_ms = dms / PASSES.get(dmeth, 1)
     achieved = nbytes(dmeth, dn) / kern_ms / 1e6
     per_row = MEASURED_TRAFFIC_PER_ROW.get((dmeth, dn))
-    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": int(per_row * M) if per_row else None,
-                "peak_source": peak_kind,
-                "kernel": f"{kernel_name(dmeth, dn)} ({dmeth}, n={dn}, m=2^25)",
-                "algorithmic_bytes_per_launch": int(nbytes(dmeth, dn)),
-                "note": "per-launch time from CUDA events around the call on its stream; Gram methods: "
-                        "call time / 2 passes"}
+    traffic = int(per_row * M) if per_row else None
+    hbm_view = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "peak_source": peak_kind}
+    kname = f"{kernel_name(dmeth, dn)} ({dmeth}, n={dn}, m=2^25)"
+    if dmeth == "tsqr" and dn > 1:
+        # the double-float Householder is bound by the FP32 pipes: 2 m n^2 FP64-equivalent
+        # flops per launch against what 128 FP32 lanes x SMs x clock deliver at 27 FP32
+        # instructions per (dot, update) pair of 4 flops
+        flops = 2.0 * M * dn * dn
+        ach = flops / (kern_ms / 1e3) / 1e12
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        clk_hz = float(clk.get("sm_max_mhz") or 2070.0) * 1e6
+        alu_peak = sms * 128 * clk_hz / (DF_INSTR_PER_PAIR / 4.0) / 1e12
+        roofline = {"bound": "alu", "achieved": round(ach, 3), "peak": round(alu_peak, 3), "unit": "TFLOP/s",
+                    "frac": round(ach / alu_peak, 4), "traffic": traffic, "peak_source": "derived",
+                    "peak_derivation": f"{sms} SMs x 128 FP32 lanes x {clk_hz / 1e6:.0f} MHz / "
+                                       f"({DF_INSTR_PER_PAIR} FP32 instructions per 4 FP64-equivalent flops)",
+                    "kernel": kname, "algorithmic_flops_per_launch": int(flops),
+                    "algorithmic_bytes_per_launch": int(nbytes(dmeth, dn)), "hbm": hbm_view,
+                    "note": "per-launch time from CUDA events around the call on its stream"}
+    else:
+        roofline = dict(hbm_view, traffic=traffic, kernel=kname,
+                        algorithmic_bytes_per_launch=int(nbytes(dmeth, dn)),
+                        note="per-launch time from CUDA events around the call on its stream; Gram methods: "
+                             "call time / 2 passes")
 
     e2e = run_e2e(args, q, lib, torch, dev, Xs, ws, wsb, stream, ls) if args.e2e_steps > 0 else None
     del ls, At, bvec
@@ -332,23 +355,27 @@ def run_ours(args, rank, world, local_rank):
 
 def run_e2e(args, q, lib, torch, dev, Xs, ws, wsb, stream, ls):
     """The same sweep through the C ABI from HOST buffers: every step copies each X from
-    pinned host memory to the device (on a copy stream, double-buffered so that the copy of
-    the next matrix overlaps the factorisations of the current one) and reads every R back,
-    all inside the timed region."""
+    pinned host memory to the device (two copy streams, one device buffer per matrix, so
+    copies overlap the factorisations still running) and reads every R back, all inside
+    the timed region."""
     import torch as _t
 
     host = {n: _t.empty(Xs[n].shape, dtype=Xs[n].dtype, pin_memory=True) for n in NS}
     for n in NS:
         host[n].copy_(Xs[n])
-    big = max(Xs[n].numel() for n in NS)
-    bufs = [_t.empty(big, dtype=_t.float64, device=dev) for _ in range(2)]
+    # one device buffer per matrix: the next step's copy of X_n waits only for this step's
+    # factorisations of X_n, so the small matrices of step k + 1 arrive while step k's
+    # widest ones are factored (copies run at full link speed only while the GPU is busy)
+    bufd = {n: _t.empty(Xs[n].numel(), dtype=_t.float64, device=dev) for n in NS}
     Rh = {n: _t.empty((n, n), dtype=_t.float64, pin_memory=True) for n in NS}
     Rd = {n: _t.empty((n, n), dtype=_t.float64, device=dev) for n in NS}
     inf = _t.zeros(2, dtype=_t.int32, device=dev)
     sptr = q._stream_ptr(stream)
-    cstream = _t.cuda.Stream(device=dev)
-    copied = [_t.cuda.Event(), _t.cuda.Event()]
-    used = [_t.cuda.Event(), _t.cuda.Event()]
+    # two copy streams, 1 GB pieces alternating between them: one stream of host -> device
+    # copies ran at ~85 GB/s on this machine, two at the full ~211 GB/s of the link
+    cstreams = [_t.cuda.Stream(device=dev), _t.cuda.Stream(device=dev)]
+    copied = {n: [_t.cuda.Event(), _t.cuda.Event()] for n in NS}  # [matrix][copy stream]
+    used = {n: _t.cuda.Event() for n in NS}
     hls = {k: (_t.empty(A.shape, dtype=A.dtype, pin_memory=True).copy_(A),
                _t.empty(b.shape, dtype=b.dtype, pin_memory=True).copy_(b), _t.empty_like(A), _t.empty_like(b), dt)
            for k, (A, b, dt) in ls.items()}
@@ -357,28 +384,32 @@ def run_e2e(args, q, lib, torch, dev, Xs, ws, wsb, stream, ls):
     h2d = sum(host[n].numel() * 8 for n in NS) + sum(v[0].numel() * v[0].element_size() + v[1].numel() *
                                                      v[1].element_size() for v in hls.values())
     d2h = sum(Rh[n].numel() * 8 * len(METHODS) for n in NS) + len(hls) * (LS_N + 1) * 8
-    seq = [0]
-    ls_copied = {k: _t.cuda.Event() for k in hls}
+    ls_copied = {k: [_t.cuda.Event(), _t.cuda.Event()] for k in hls}
     ls_used = {k: _t.cuda.Event() for k in hls}
 
     def copy_in(dst, src):
-        """Host -> device in 1 GB pieces on the current stream: single pinned copies of
-        several GB ran at well under half the link rate on this machine."""
+        """Host -> device in 1 GB pieces alternating over the two copy streams."""
         d, h = dst.view(-1), src.reshape(-1)
         ch = (1 << 30) // h.element_size()
-        for i in range(0, h.numel(), ch):
-            d[i:i + ch].copy_(h[i:i + ch], non_blocking=True)
+        for k, i in enumerate(range(0, h.numel(), ch)):
+            with _t.cuda.stream(cstreams[k % 2]):
+                d[i:i + ch].copy_(h[i:i + ch], non_blocking=True)
+
+    def copies_wait(ev):
+        for cs in cstreams:
+            cs.wait_event(ev)
+
+    def copies_done(evs):
+        for cs, e in zip(cstreams, evs):
+            e.record(cs)
+            stream.wait_event(e)
 
     def step():
         for n in NS:
-            b = seq[0] % 2
-            seq[0] += 1
-            dst = bufs[b][: host[n].numel()]
-            cstream.wait_event(used[b])
-            with _t.cuda.stream(cstream):
-                copy_in(dst, host[n])
-                copied[b].record(cstream)
-            stream.wait_event(copied[b])
+            dst = bufd[n]
+            copies_wait(used[n])
+            copy_in(dst, host[n])
+            copies_done(copied[n])
             X = dst.data_ptr()
             for meth in METHODS:
                 if meth == "tsqr":
@@ -390,15 +421,16 @@ def run_e2e(args, q, lib, torch, dev, Xs, ws, wsb, stream, ls):
                     lib.ql_svqb_qless(M, n, X, q.QL_F64, M, Rd[n].data_ptr(), n, None, 0.0, inf.data_ptr(),
                                       ws.data_ptr(), wsb, sptr)
                 Rh[n].copy_(Rd[n], non_blocking=True)
-            used[b].record(stream)
+            used[n].record(stream)
         for name, (Ah, bh, Ad, bd, dt) in hls.items():  # least squares: [A b] from host, x back
-            cstream.wait_event(ls_used[name])
-            with _t.cuda.stream(cstream):  # queued behind the sweep's copies: overlaps its last factorisations
-                copy_in(Ad, Ah)
-                copy_in(bd, bh)
-                ls_copied[name].record(cstream)
+            copies_wait(ls_used[name])  # queued behind the sweep's copies: overlaps its last factorisations
+            copy_in(Ad, Ah)
+            copy_in(bd, bh)
+            for cs, e in zip(cstreams, ls_copied[name]):
+                e.record(cs)
         for name, (Ah, bh, Ad, bd, dt) in hls.items():
-            stream.wait_event(ls_copied[name])
+            for e in ls_copied[name]:
+                stream.wait_event(e)
             lib.ql_lstsq_qless(LS_M, LS_N, Ad.data_ptr(), LS_M, bd.data_ptr(), dt, q.QL_TSQR, xd.data_ptr(),
                                xd[LS_N:].data_ptr(), None, inf.data_ptr(), ws.data_ptr(), wsb, sptr)
             ls_used[name].record(stream)
@@ -408,20 +440,21 @@ def run_e2e(args, q, lib, torch, dev, Xs, ws, wsb, stream, ls):
     _t.cuda.synchronize()
     e0, e1 = _t.cuda.Event(enable_timing=True), _t.cuda.Event(enable_timing=True)
     e0.record(stream)
-    cstream.wait_event(e0)
+    copies_wait(e0)
     for _ in range(args.e2e_steps):
         step()
-    stream.wait_stream(cstream)
+    for cs in cstreams:
+        stream.wait_stream(cs)
     e1.record(stream)
     _t.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.e2e_steps
     bytes_step = sum(8.0 * M * n * len(METHODS) for n in NS) + 12.0 * LS_M * (LS_N + 1)
-    del host, bufs, hls
+    del host, bufd, hls
     return {"value": round(bytes_step / (ms / 1e3) / 1e9, 2), "unit": "GB/s", "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h), "ms_per_step": round(ms, 3),
             "note": "each X (and each [A b]) copied host->device once per step from pinned memory in 1 GB "
-                    "pieces on a second stream (double-buffered, overlapping the previous matrix's "
-                    "factorisations); every R and x read back"}
+                    "pieces alternating over two copy streams into its own device buffer, so copies overlap "
+                    "the factorisations still running (also the previous step's); every R and x read back"}
 
 
 # ------------------------------------------------------------------ batched and serving forms
