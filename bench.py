@@ -74,6 +74,8 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--no-batched", dest="batched", action="store_false")
     p.add_argument("--no-serving", dest="serving", action="store_false")
+    p.add_argument("--no-next", dest="next_rows", action="store_false",
+                   help="skip the shifted Cholesky-QR3 measurement (kappa = 1e8)")
     p.add_argument("--case", default=None,
                    help="METHOD:N:M -- time one call shape alone (profiling aid; prints its own JSON line)")
     return p.parse_args()
@@ -324,6 +326,12 @@ def run_ours(args, rank, world, local_rank):
     del Xs
     torch.cuda.empty_cache()
     extra = {}
+    if args.next_rows:
+        try:
+            extra["scholqr3"] = run_scholqr3(q, lib, torch, dev, stream)
+        except Exception as exc:
+            extra["scholqr3"] = {"error": repr(exc)[:300]}
+        torch.cuda.empty_cache()
     if args.batched:
         try:
             extra["batched"] = run_batched(q, lib, torch, dev, stream)
@@ -455,6 +463,40 @@ def run_e2e(args, q, lib, torch, dev, Xs, ws, wsb, stream, ls):
             "note": "each X (and each [A b]) copied host->device once per step from pinned memory in 1 GB "
                     "pieces alternating over two copy streams into its own device buffer, so copies overlap "
                     "the factorisations still running (also the previous step's); every R and x read back"}
+
+
+# ------------------------------------------------------------------ shifted Cholesky-QR3
+
+
+def run_scholqr3(q, lib, torch, dev, stream, reps=3):
+    """Shifted Cholesky-QR3 on the condition sweep's kappa = 1e8 inputs (m = 2^25, beyond
+    Cholesky-QR2's range): time per call, effective GB/s, the status of Cholesky-QR2 on the
+    same X, and the relative difference of R from TSQR's."""
+    from paper_2603_20889_gb300 import synth
+
+    out = {"workload": "X = G S, m = 2^25, kappa = 1e8, FP64 storage", "calls": []}
+    for n in (16, 64):
+        X = synth.conditioned_device(M, n, 1e8, seed=2000 + n, device=dev)
+        Xt = X.T
+        ws = q.workspace(q.QL_AUTO, M, n, q.QL_F64, dev)
+        R3, inf3 = q.scholqr3_qless(Xt, ws=ws)
+        Rc, infc = q.cholqr2_qless(Xt, ws=ws)
+        Rt, _ = q.tsqr_qless(Xt, ws=ws)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            q.scholqr3_qless(Xt, R3, inf3, ws)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        diff = float(torch.linalg.norm(R3 - Rt) / torch.linalg.norm(Rt))
+        out["calls"].append({"n": n, "ms": round(ms, 3), "eff_gbs": round(8.0 * M * n / ms / 1e6, 1),
+                             "status": inf3.tolist(), "cholqr2_status": infc.tolist(),
+                             "rel_diff_vs_tsqr": diff, "tolerance_1e-13_n_kappa": 1e-13 * n * 1e8})
+        del X, Xt, ws
+        torch.cuda.empty_cache()
+    return out
 
 
 # ------------------------------------------------------------------ batched and serving forms

@@ -61,7 +61,7 @@ typedef int32_t ql_dtype;
 enum { QL_F64 = 0, QL_F32 = 1 };
 
 typedef int32_t ql_method;
-enum { QL_TSQR = 0, QL_CHOLQR2 = 1, QL_SVQB2 = 2, QL_AUTO = 3 };
+enum { QL_TSQR = 0, QL_CHOLQR2 = 1, QL_SVQB2 = 2, QL_AUTO = 3, QL_SCHOLQR3 = 4 };
 
 /* Arithmetic of the m-proportional loops.
  *   QL_ARITH_DF  (default) double-float on the FP32 pipes; the kernels check that every
@@ -126,6 +126,19 @@ ql_status ql_cholqr2_qless(int64_t m, int64_t n, const void* X, ql_dtype dtype, 
                            int64_t ldr, int32_t* info, void* ws, size_t ws_bytes, void* stream);
 
 /*
+ * Q-less shifted Cholesky-QR3 (the variant Sec. 1 cites for ill-conditioned X, robust for
+ * kappa(X) up to about u^{-1/2}): three Gram passes over X.
+ *   pass 1: C1 = X^T X, s = 11 (m n + n (n + 1)) u ||X||_F^2 with u = 2^-53 and
+ *           ||X||_F^2 = trace(C1) standing in for ||X||_2^2 (an upper bound), R1 = chol(C1 + s I);
+ *   pass 2: Y = X R1^{-1} formed tile by tile, R2 = chol(Y^T Y);
+ *   pass 3: Y = X (R2 R1)^{-1}, R3 = chol(Y^T Y);  R = R3 R2 R1.
+ * Arguments, workspace and outputs as ql_cholqr2_qless.  A non-positive pivot sets info =
+ * {QL_ERR_NOT_SPD, pivot + 1000 (pass - 1)} and R = NaN.
+ */
+ql_status ql_scholqr3_qless(int64_t m, int64_t n, const void* X, ql_dtype dtype, int64_t ldx, double* R,
+                            int64_t ldr, int32_t* info, void* ws, size_t ws_bytes, void* stream);
+
+/*
  * Q-less SVQB2 (Sec. 3.1, SVQB applied twice): C = X^T X = U L U^T (FP64 Jacobi on the
  * device), B1 = U L^{-1/2} with eigenvalues below rank_tol * lambda_max treated as zero
  * (rank_tol <= 0 selects n * 2^-52); second pass on X B1 (formed tile by tile); then
@@ -141,7 +154,7 @@ ql_status ql_svqb_qless(int64_t m, int64_t n, const void* X, ql_dtype dtype, int
  * the extended matrix [A b] gives R_ext = [[R, z], [0, rho]], then x = R^{-1} z (FP64
  * back-substitution on the device) and ||b - A x|| = rho.  A is m x n (lda >= m), b has m
  * entries (contiguous), both of `dtype`; [A b] is read in place, never copied.  method is
- * QL_TSQR or QL_CHOLQR2 (QL_AUTO = TSQR).  x (device double[n]), resnorm (device double[1]);
+ * QL_TSQR, QL_CHOLQR2 or QL_SCHOLQR3 (QL_AUTO: the tuner's choice, TSQR without a table).  x (device double[n]), resnorm (device double[1]);
  * Rext (nullable device double (n+1) x (n+1), ld n+1).  1 <= n <= 63.  A zero diagonal
  * entry of R sets info = {QL_ERR_NOT_SPD, i} and x = NaN.
  */

@@ -33,6 +33,7 @@ def _load():
             "qo_gram": [_I64, _I64, _DP, _I64, _DP, _I64],
             "qo_cholesky_upper": [_I64, _DP, _I64, _DP, _I64],
             "qo_cholqr2": [_I64, _I64, _DP, _I64, _DP, _I64, _DP],
+            "qo_scholqr3": [_I64, _I64, _DP, _I64, _DP, _I64],
             "qo_jacobi_eig": [_I64, _DP, _I64, _DP, _DP, _I64],
             "qo_svqb2": [_I64, _I64, _DP, _I64, _DP, _I64, _DP],
             "qo_back_substitution": [_I64, _DP, _I64, _DP, _DP],
@@ -99,6 +100,15 @@ def cholqr2(X):
     R1 = np.zeros((n, n), order="F")
     info = _load().qo_cholqr2(m, n, _p(X), max(m, 1), _p(R), n, _p(R1))
     return R, R1, info
+
+
+def scholqr3(X):
+    """(R, info) of shifted Cholesky-QR3; info: j+1, 1000+j+1 or 2000+j+1 by failing pass."""
+    X = _f64(X)
+    m, n = X.shape
+    R = np.zeros((n, n), order="F")
+    info = _load().qo_scholqr3(m, n, _p(X), max(m, 1), _p(R), n)
+    return R, info
 
 
 def jacobi_eig(C):

@@ -18,6 +18,8 @@
  *   qo_gram            C = X^T X, the first step of Algorithm 1.
  *   qo_cholesky_upper  R^T R = C (the "chol" of Algorithm 1, steps 2 and 4).
  *   qo_cholqr2         Algorithm 1 (Q-less Cholesky-QR2), step by step.
+ *   qo_scholqr3        shifted Cholesky-QR3, the ill-conditioned variant Sec. 1 cites, in the
+ *                      published form: chol(X^T X + s I), then Cholesky-QR twice.
  *   qo_jacobi_eig      C = U diag(lambda) U^T (the eigendecomposition that SVQB uses in
  *                      place of chol, Sec. 3.1).
  *   qo_svqb2           SVQB applied twice (Sec. 3.1): B = U Lambda^{-1/2}, X B = Q, and the
@@ -179,6 +181,50 @@ int qo_cholqr2(int64_t m, int64_t n, const double* X, int64_t ldx, double* R, in
     for (size_t k = 0; k < nn; ++k) R1_out[k] = R1[k];
 done:
   free(C); free(R1); free(R2); free(Y);
+  return info;
+}
+
+/*
+ * Shifted Cholesky-QR3:
+ *   C <- X^T X;  s <- 11 (m n + n (n + 1)) u ||X||_F^2 with u = 2^-53 and ||X||_F^2 =
+ *   trace(C) (an upper bound of ||X||_2^2);  R1 <- chol(C + s I);  Y1 <- X / R1;
+ *   R2 <- chol(Y1^T Y1);  Y2 <- Y1 / R2;  R3 <- chol(Y2^T Y2);  R <- R3 R2 R1.
+ * Returns the chol info of the failing step: j+1, 1000 + j+1 or 2000 + j+1.
+ */
+int qo_scholqr3(int64_t m, int64_t n, const double* X, int64_t ldx, double* R, int64_t ldr) {
+  if (m < 0 || n < 1 || ldx < (m > 1 ? m : 1) || ldr < n) return -1;
+  size_t nn = (size_t)n * (size_t)n, mn = (size_t)(m > 0 ? m : 1) * (size_t)n;
+  int64_t ldy = m > 1 ? m : 1;
+  double* C = (double*)malloc(nn * sizeof(double));
+  double* R1 = (double*)malloc(nn * sizeof(double));
+  double* R2 = (double*)malloc(nn * sizeof(double));
+  double* R3 = (double*)malloc(nn * sizeof(double));
+  double* T = (double*)malloc(nn * sizeof(double));
+  double* Y1 = (double*)malloc(mn * sizeof(double));
+  double* Y2 = (double*)malloc(mn * sizeof(double));
+  int info = -1;
+  if (!C || !R1 || !R2 || !R3 || !T || !Y1 || !Y2) goto done;
+  qo_gram(m, n, X, ldx, C, n);
+  {
+    acc_t tr = 0.0L;
+    for (int64_t j = 0; j < n; ++j) tr += AT(C, n, j, j);
+    double shift = (double)(11.0L * ((acc_t)m * (acc_t)n + (acc_t)n * (acc_t)(n + 1)) * ldexpl(1.0L, -53) * tr);
+    for (int64_t j = 0; j < n; ++j) AT(C, n, j, j) += shift;
+  }
+  info = qo_cholesky_upper(n, C, n, R1, n);
+  if (info) goto done;
+  right_upper_solve(m, n, X, ldx, R1, n, Y1);
+  qo_gram(m, n, Y1, ldy, C, n);
+  info = qo_cholesky_upper(n, C, n, R2, n);
+  if (info) { info += 1000; goto done; }
+  right_upper_solve(m, n, Y1, ldy, R2, n, Y2);
+  qo_gram(m, n, Y2, ldy, C, n);
+  info = qo_cholesky_upper(n, C, n, R3, n);
+  if (info) { info += 2000; goto done; }
+  upper_product(n, R2, n, R1, n, T, n);
+  upper_product(n, R3, n, T, n, R, ldr);
+done:
+  free(C); free(R1); free(R2); free(R3); free(T); free(Y1); free(Y2);
   return info;
 }
 

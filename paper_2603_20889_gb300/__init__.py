@@ -23,7 +23,7 @@ LIB_PATH = os.path.join(HERE, "_lib", "libqless.so")
 QL_OK, QL_ERR_ARG, QL_ERR_ALIGN, QL_ERR_WORKSPACE, QL_ERR_CUDA = 0, 1, 2, 3, 4
 QL_ERR_NOT_SPD, QL_ERR_TIMEOUT, QL_ERR_NONFINITE, QL_ERR_BUDGET, QL_ERR_BUSY, QL_ERR_UNKNOWN = 5, 6, 7, 8, 9, 10
 QL_F64, QL_F32 = 0, 1
-QL_TSQR, QL_CHOLQR2, QL_SVQB2, QL_AUTO = 0, 1, 2, 3
+QL_TSQR, QL_CHOLQR2, QL_SVQB2, QL_AUTO, QL_SCHOLQR3 = 0, 1, 2, 3, 4
 QL_ARITH_DF, QL_ARITH_F64 = 0, 1
 
 STATUS_NAMES = {0: "QL_OK", 1: "QL_ERR_ARG", 2: "QL_ERR_ALIGN", 3: "QL_ERR_WORKSPACE", 4: "QL_ERR_CUDA",
@@ -40,6 +40,7 @@ SIGNATURES = {
     "ql_tsqr_qless": (_i32, [_i64, _i64, _vp, _i32, _i64, _dp, _i64, _vp, _vp, _sz, _vp]),
     "ql_tsqr_qless_noalloc": (_i32, [_i64, _i64, _vp, _i32, _i64, _dp, _i64, _vp, _vp]),
     "ql_cholqr2_qless": (_i32, [_i64, _i64, _vp, _i32, _i64, _dp, _i64, _vp, _vp, _sz, _vp]),
+    "ql_scholqr3_qless": (_i32, [_i64, _i64, _vp, _i32, _i64, _dp, _i64, _vp, _vp, _sz, _vp]),
     "ql_svqb_qless": (_i32, [_i64, _i64, _vp, _i32, _i64, _dp, _i64, _dp, _f64, _vp, _vp, _sz, _vp]),
     "ql_lstsq_qless": (_i32, [_i64, _i64, _vp, _i64, _vp, _i32, _i32, _dp, _dp, _dp, _vp, _vp, _sz, _vp]),
     "ql_batch_workspace_bytes": (_sz, [_i32, _vp]),
@@ -197,6 +198,19 @@ def cholqr2_qless(X, R=None, info=None, ws=None, stream=None):
     st = load_library().ql_cholqr2_qless(m, n, X.data_ptr(), dt, ld, R.data_ptr(), R.stride(1) if n > 1 else n,
                                          info.data_ptr(), ws.data_ptr(), ws.numel(), _stream_ptr(stream))
     _check(st, "ql_cholqr2_qless")
+    return R, info
+
+
+def scholqr3_qless(X, R=None, info=None, ws=None, stream=None):
+    """R of X by Q-less shifted Cholesky-QR3 (three Gram passes).  Returns (R, info)."""
+    torch = _torch()
+    m, n, ld, dt = _colmajor(X)
+    R = R if R is not None else torch.empty((n, n), dtype=torch.float64, device=X.device).T
+    info = info if info is not None else torch.zeros(2, dtype=torch.int32, device=X.device)
+    ws = ws if ws is not None else workspace(QL_SCHOLQR3, m, n, dt, X.device)
+    st = load_library().ql_scholqr3_qless(m, n, X.data_ptr(), dt, ld, R.data_ptr(), R.stride(1) if n > 1 else n,
+                                          info.data_ptr(), ws.data_ptr(), ws.numel(), _stream_ptr(stream))
+    _check(st, "ql_scholqr3_qless")
     return R, info
 
 

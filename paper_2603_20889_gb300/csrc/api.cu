@@ -52,6 +52,7 @@ size_t ql_workspace_bytes(ql_method method, int64_t m, int64_t n, ql_dtype dtype
   switch (method) {
     case QL_TSQR: return t;
     case QL_CHOLQR2:
+    case QL_SCHOLQR3:
     case QL_SVQB2: return g;
     case QL_AUTO: return t > g ? t : g;
     default: return 0;
@@ -115,6 +116,11 @@ ql_status ql_cholqr2_qless(int64_t m, int64_t n, const void* X, ql_dtype dtype, 
   return gram_entry(QL_CHOLQR2, m, n, X, dtype, ldx, R, ldr, nullptr, 0.0, info, ws, ws_bytes, stream);
 }
 
+ql_status ql_scholqr3_qless(int64_t m, int64_t n, const void* X, ql_dtype dtype, int64_t ldx, double* R,
+                            int64_t ldr, int32_t* info, void* ws, size_t ws_bytes, void* stream) {
+  return gram_entry(QL_SCHOLQR3, m, n, X, dtype, ldx, R, ldr, nullptr, 0.0, info, ws, ws_bytes, stream);
+}
+
 ql_status ql_svqb_qless(int64_t m, int64_t n, const void* X, ql_dtype dtype, int64_t ldx, double* R,
                         int64_t ldr, double* Z, double rank_tol, int32_t* info, void* ws, size_t ws_bytes,
                         void* stream) {
@@ -148,7 +154,7 @@ ql_status ql_lstsq_qless(int64_t m, int64_t n, const void* A, int64_t lda, const
     c.stream = (cudaStream_t)stream;
     return tsqr_launch(c, current_arith());
   }
-  if (method == QL_CHOLQR2 || method == QL_SVQB2) {
+  if (method == QL_CHOLQR2 || method == QL_SVQB2 || method == QL_SCHOLQR3) {
     GramCall c;
     c.m = m;
     c.n = (int)n + 1;

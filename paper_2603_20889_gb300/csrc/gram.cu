@@ -46,7 +46,7 @@ size_t gram_workspace_bytes(int n) {
 
 ql_status gram_launch(const GramCall& c, ql_arith arith) {
   if (c.n < 1 || c.n > kMaxN) return QL_ERR_ARG;
-  if (c.method != QL_CHOLQR2 && c.method != QL_SVQB2) return QL_ERR_ARG;
+  if (c.method != QL_CHOLQR2 && c.method != QL_SVQB2 && c.method != QL_SCHOLQR3) return QL_ERR_ARG;
   if (!c.ws || c.ws_bytes < gram_layout(c.n, nullptr, nullptr)) return QL_ERR_WORKSPACE;
   GramWs w;
   gram_layout(c.n, &w, c.ws);

@@ -29,7 +29,7 @@ struct GramArgs {
   int n;
   int64_t tiles;
   int pass;    // 1 or 2
-  int method;  // QL_CHOLQR2 or QL_SVQB2
+  int method;  // QL_CHOLQR2, QL_SVQB2 or QL_SCHOLQR3
   int gated;
   int epilogue;
   GramWs w;
@@ -71,8 +71,8 @@ __global__ void __launch_bounds__(GramShape<NC>::T, 1) gram_kernel(GramArgs<S> a
   const int tid = threadIdx.x, n = a.n;
 
   if (a.gated && *(volatile int*)&a.w.flags[0] == 0) return;
-  if (Ar::kRangeChecked && a.pass == 2 && *(volatile int*)&a.w.flags[0] != 0) return;  // FP64 redoes it
-  if (a.pass == 2 && *(volatile int*)&a.w.flags[1] != 0) {  // first pass broke down
+  if (Ar::kRangeChecked && a.pass >= 2 && *(volatile int*)&a.w.flags[0] != 0) return;  // FP64 redoes it
+  if (a.pass >= 2 && *(volatile int*)&a.w.flags[1] != 0) {  // first pass broke down
     if (blockIdx.x == 0) write_nan_outputs(a, T);
     return;
   }
@@ -263,15 +263,34 @@ QL_DEV void gram_finish(const GramArgs<S>& a, unsigned char* smem, const int* co
   __syncthreads();
   double* keep = a.w.keep;  // [0]: R1 or S1, [1]: M (R1^{-1} or B1)
   const int nn = n * n;
-  if (a.method == QL_CHOLQR2) {
+  if (a.method == QL_CHOLQR2 || a.method == QL_SCHOLQR3) {
+    const int last = a.method == QL_SCHOLQR3 ? 3 : 2;
+    if (a.method == QL_SCHOLQR3 && a.pass == 1) {
+      // shifted Cholesky: C1 + s I with s = 11 (m n + n (n + 1)) u ||X||_F^2, u = 2^-53
+      if (tid == 0) {
+        double tr = 0.0;
+        for (int i = 0; i < n; ++i) tr += Cs[i * LE + i];
+        const double sh = 11.0 * ((double)a.m * n + (double)n * (n + 1)) * 0x1p-53 * tr;
+        for (int i = 0; i < n; ++i) Cs[i * LE + i] += sh;
+      }
+      __syncthreads();
+    }
     int fail = chol_upper_inplace<T>(Cs, LE, n, sflag);
     if (fail) {
-      if (a.pass == 1) a.w.flags[1] = 1;
+      if (a.pass < last) a.w.flags[1] = 1;
       write_nan_outputs(a, T);
-      write_info(a.info, QL_ERR_NOT_SPD, fail + (a.pass == 2 ? 1000 : 0));
+      write_info(a.info, QL_ERR_NOT_SPD, fail + 1000 * (a.pass - 1));
       return;
     }
-    if (a.pass == 1) {
+    if (a.pass < last) {
+      // carry R (= R1, or R2 R1) and its inverse, the next pass's M, to the next pass
+      if (a.pass > 1) {
+        for (int e = tid; e < nn; e += T) Us[(e / n) * LE + e % n] = __ldcg(keep + e);
+        __syncthreads();
+        upper_times_upper<T>(Cs, LE, Us, LE, Ps, LE, n);
+        for (int e = tid; e < nn; e += T) Cs[(e / n) * LE + e % n] = Ps[(e / n) * LE + e % n];
+        __syncthreads();
+      }
       tri_upper_inverse<T>(Cs, LE, Us, LE, n);
       for (int e = tid; e < nn; e += T) {
         keep[e] = Cs[(e / n) * LE + e % n];
@@ -279,7 +298,7 @@ QL_DEV void gram_finish(const GramArgs<S>& a, unsigned char* smem, const int* co
       }
       return;
     }
-    // pass 2: R = R2 R1
+    // last pass: R = R_last (R_prev ... R1)
     for (int e = tid; e < nn; e += T) Us[(e / n) * LE + e % n] = __ldcg(keep + e);
     __syncthreads();
     upper_times_upper<T>(Cs, LE, Us, LE, Ps, LE, n);
@@ -339,8 +358,8 @@ __global__ void __launch_bounds__(256, 1) gram_tc_kernel(GramArgs<S> a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int tid = threadIdx.x, n = a.n, lane = tid & 31, warp = tid >> 5;
 
-  if (a.pass == 2 && *(volatile int*)&a.w.flags[0] != 0) return;  // the FP64 launches redo it
-  if (a.pass == 2 && *(volatile int*)&a.w.flags[1] != 0) {         // first pass broke down
+  if (a.pass >= 2 && *(volatile int*)&a.w.flags[0] != 0) return;  // the FP64 launches redo it
+  if (a.pass >= 2 && *(volatile int*)&a.w.flags[1] != 0) {         // first pass broke down
     if (blockIdx.x == 0) write_nan_outputs(a, T);
     return;
   }
@@ -750,8 +769,8 @@ __global__ void __launch_bounds__(256, 1) gram_umma_kernel(GramArgs<S> a) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, n = a.n, lane = tid & 31, warp = tid >> 5;
 
-  if (a.pass == 2 && *(volatile int*)&a.w.flags[0] != 0) return;  // the FP64 launches redo it
-  if (a.pass == 2 && *(volatile int*)&a.w.flags[1] != 0) {         // first pass broke down
+  if (a.pass >= 2 && *(volatile int*)&a.w.flags[0] != 0) return;  // the FP64 launches redo it
+  if (a.pass >= 2 && *(volatile int*)&a.w.flags[1] != 0) {         // first pass broke down
     if (blockIdx.x == 0) write_nan_outputs(a, T);
     return;
   }
@@ -1239,7 +1258,7 @@ ql_status gram_launch_one(const GramCall& c, const GramWs& w, int pass, int gate
   return cudaPeekAtLastError() == cudaSuccess ? QL_OK : QL_ERR_CUDA;
 }
 
-// Both passes of one method for one (storage, arithmetic) pair.
+// All passes of one method (two, three for shifted Cholesky-QR3) for one (storage, arithmetic) pair.
 template <typename S, typename Ar>
 ql_status gram_dispatch(const GramCall& c, const GramWs& w, int gated) {
   auto two = [&](auto nc_tag) -> ql_status {
@@ -1251,19 +1270,25 @@ ql_status gram_dispatch(const GramCall& c, const GramWs& w, int gated) {
         if (NC == 64 && umma_gram_enabled()) {
           ql_status st = gram_umma_launch_one<NC, S, kXNone>(c, w, 1);
           if (st) return st;
-          if (c.method == QL_CHOLQR2) return gram_umma_launch_one<NC, S, kXUpper>(c, w, 2);
-          return gram_umma_launch_one<NC, S, kXFull>(c, w, 2);
+          if (c.method == QL_SVQB2) return gram_umma_launch_one<NC, S, kXFull>(c, w, 2);
+          st = gram_umma_launch_one<NC, S, kXUpper>(c, w, 2);
+          if (st || c.method != QL_SCHOLQR3) return st;
+          return gram_umma_launch_one<NC, S, kXUpper>(c, w, 3);
         }
         ql_status st = gram_tc_launch_one<NC, S, kXNone>(c, w, 1);
         if (st) return st;
-        if (c.method == QL_CHOLQR2) return gram_tc_launch_one<NC, S, kXUpper>(c, w, 2);
-        return gram_tc_launch_one<NC, S, kXFull>(c, w, 2);
+        if (c.method == QL_SVQB2) return gram_tc_launch_one<NC, S, kXFull>(c, w, 2);
+        st = gram_tc_launch_one<NC, S, kXUpper>(c, w, 2);
+        if (st || c.method != QL_SCHOLQR3) return st;
+        return gram_tc_launch_one<NC, S, kXUpper>(c, w, 3);
       }
     }
     ql_status st = gram_launch_one<NC, S, Ar, kXNone>(c, w, 1, gated);
     if (st) return st;
-    if (c.method == QL_CHOLQR2) return gram_launch_one<NC, S, Ar, kXUpper>(c, w, 2, gated);
-    return gram_launch_one<NC, S, Ar, kXFull>(c, w, 2, gated);
+    if (c.method == QL_SVQB2) return gram_launch_one<NC, S, Ar, kXFull>(c, w, 2, gated);
+    st = gram_launch_one<NC, S, Ar, kXUpper>(c, w, 2, gated);
+    if (st || c.method != QL_SCHOLQR3) return st;
+    return gram_launch_one<NC, S, Ar, kXUpper>(c, w, 3, gated);
   };
   const int n = c.n;
   if (n <= 1) return two(std::integral_constant<int, 1>{});

@@ -86,6 +86,36 @@ def test_gram_methods_match_oracle(m, n, kappa, arith, method):
     assert err <= oracle.tolerance(n, kappa), (err, oracle.tolerance(n, kappa))
 
 
+@pytest.mark.parametrize("arith", ARITHS)
+@pytest.mark.parametrize("m,n,kappa", [
+    (1000, 1, 1.0), (4097, 5, 1e8), (100003, 8, 1e6), (30011, 16, 1e8), (20011, 31, 1e4),
+    (50000, 32, 1e8), (12000, 64, 1e8), (20000, 48, 1e10),
+])
+def test_scholqr3_matches_oracle(m, n, kappa, arith):
+    """Shifted Cholesky-QR3 (three Gram passes) against the Householder R, up to kappa = 1e10
+    (beyond Cholesky-QR2's range); backward error ||R^T R - X^T X|| / ||X||^2 as well."""
+    import paper_2603_20889_gb300 as q
+
+    _arith(q, arith)
+    X, R_ref = case(m, n, kappa, m % 991 + n)
+    R, info = q.scholqr3_qless(to_dev(X))
+    R = to_host(R)
+    assert info_of(info) == [0, 0]
+    err = oracle.rel_err(R, R_ref)
+    assert err <= oracle.tolerance(n, kappa), (err, oracle.tolerance(n, kappa))
+    assert np.linalg.norm(R.T @ R - X.T @ X) <= 1e-13 * n * np.linalg.norm(X) ** 2
+
+
+def test_scholqr3_breakdown_reports_pass_and_pivot():
+    """A zero column survives the shifted first pass and breaks the second at its pivot."""
+    import paper_2603_20889_gb300 as q
+
+    x = synth.gaussian(4000, 3, seed=9)
+    R, info = q.scholqr3_qless(to_dev(np.column_stack([x, np.zeros(4000)])))
+    assert info_of(info) == [q.QL_ERR_NOT_SPD, 1004]
+    assert np.all(np.isnan(to_host(R)))
+
+
 def test_svqb_z_factor():
     import paper_2603_20889_gb300 as q
 
@@ -97,14 +127,15 @@ def test_svqb_z_factor():
     assert np.linalg.norm(Z.T @ Z - G) <= 1e-12 * np.linalg.norm(G)
 
 
-@pytest.mark.parametrize("method", ["tsqr", "cholqr2", "svqb2"])
+@pytest.mark.parametrize("method", ["tsqr", "cholqr2", "svqb2", "scholqr3"])
 @pytest.mark.parametrize("m,n", [(65536, 8), (131072, 16), (32768, 64)])
 def test_hadamard_exact(m, n, method):
     """X = H[:, :n] R0 exactly, so R = sqrt(m) R0: an exact expected value at any size."""
     import paper_2603_20889_gb300 as q
 
     X, R_exact = synth.hadamard_case(m, n, seed=3)
-    fn = {"tsqr": q.tsqr_qless, "cholqr2": q.cholqr2_qless, "svqb2": lambda x: q.svqb_qless(x)[::2]}[method]
+    fn = {"tsqr": q.tsqr_qless, "cholqr2": q.cholqr2_qless, "svqb2": lambda x: q.svqb_qless(x)[::2],
+          "scholqr3": q.scholqr3_qless}[method]
     R, info = fn(to_dev(X))
     assert info_of(info) == [0, 0]
     kappa = np.linalg.cond(R_exact)
@@ -197,7 +228,7 @@ def test_cholqr2_breakdown_reports_pivot():
     assert np.all(np.isnan(to_host(R)))
 
 
-@pytest.mark.parametrize("method", ["tsqr", "cholqr2"])
+@pytest.mark.parametrize("method", ["tsqr", "cholqr2", "scholqr3"])
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 @pytest.mark.parametrize("m", [60013, 60000])  # unaligned columns; 16-byte aligned columns (bulk tile copies)
 def test_lstsq_matches_oracle(method, dtype, m):
@@ -209,7 +240,8 @@ def test_lstsq_matches_oracle(method, dtype, m):
     x_ref, rho_ref, Re_ref, info_ref = oracle.lstsq(A.astype(np.float64), b.astype(np.float64))
     assert info_ref == 0
     x, rn, Rext, info = q.lstsq_qless(to_dev(A), torch.from_numpy(b).cuda(),
-                                      method=q.QL_TSQR if method == "tsqr" else q.QL_CHOLQR2, want_rext=True)
+                                      method={"tsqr": q.QL_TSQR, "cholqr2": q.QL_CHOLQR2,
+                                              "scholqr3": q.QL_SCHOLQR3}[method], want_rext=True)
     assert info_of(info) == [0, 0]
     x = to_host(x)
     kappa = 1e3

@@ -241,6 +241,39 @@ def test_svqb2_rank_deficient_gives_zero_diagonal():
     assert np.linalg.norm(R.T @ R - X.T @ X) <= 1e-12 * np.linalg.norm(X) ** 2
 
 
+@pytest.mark.parametrize("kappa", [1.0, 1e4, 1e8, 1e10])
+def test_scholqr3_reaches_the_householder_r(kappa):
+    """Shifted Cholesky-QR3 has the exact R in exact arithmetic (the shift only changes the
+    first, preconditioning pass), and stays backward stable far past Cholesky-QR2's range."""
+    n = 12
+    X = synth.conditioned(3000, n, kappa, seed=7)
+    R_h = oracle.householder_r(X)
+    R_s, info = oracle.scholqr3(X)
+    assert info == 0
+    assert oracle.rel_err(R_s, R_h) <= min(oracle.tolerance(n, kappa), 1e-9)
+    assert np.linalg.norm(R_s.T @ R_s - X.T @ X) <= 1e-14 * n * np.linalg.norm(X) ** 2
+    assert np.all(np.diag(R_s) > 0.0) and np.all(np.tril(R_s, -1) == 0.0)
+
+
+def test_scholqr3_hadamard_exact_and_scaling():
+    """X = H[:, :n] R0 gives R = sqrt(m) R0 exactly; X 2^k gives R 2^k bitwise (the shift
+    scales with ||X||^2, every step commutes with a power-of-two scaling)."""
+    X, R_exact = synth.hadamard_case(4096, 8, seed=2)
+    R, info = oracle.scholqr3(X)
+    assert info == 0
+    assert oracle.rel_err(R, R_exact) <= oracle.tolerance(8, np.linalg.cond(R_exact))
+    R_scaled, info2 = oracle.scholqr3(X * 2.0 ** -37)
+    assert info2 == 0 and np.array_equal(R_scaled, R * 2.0 ** -37)
+
+
+def test_scholqr3_breakdown_index_on_rank_deficiency():
+    """A zero column leaves chol(C + s I) positive (the shift), so the breakdown comes in
+    the second pass, at the zero column's pivot: 1000 + 4."""
+    X = np.column_stack([synth.gaussian(200, 3, seed=5), np.zeros(200)])
+    _, info = oracle.scholqr3(X)
+    assert info == 1004
+
+
 # ---------------------------------------------------------------- least squares
 
 
