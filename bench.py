@@ -75,7 +75,7 @@ def parse():
     p.add_argument("--no-batched", dest="batched", action="store_false")
     p.add_argument("--no-serving", dest="serving", action="store_false")
     p.add_argument("--no-next", dest="next_rows", action="store_false",
-                   help="skip the shifted Cholesky-QR3 measurement (kappa = 1e8)")
+                   help="skip the shifted Cholesky-QR3 (kappa = 1e8) and Q = X R^-1 measurements")
     p.add_argument("--case", default=None,
                    help="METHOD:N:M -- time one call shape alone (profiling aid; prints its own JSON line)")
     return p.parse_args()
@@ -332,6 +332,11 @@ def run_ours(args, rank, world, local_rank):
         except Exception as exc:
             extra["scholqr3"] = {"error": repr(exc)[:300]}
         torch.cuda.empty_cache()
+        try:
+            extra["q_from_r"] = run_qform(q, lib, torch, dev, stream)
+        except Exception as exc:
+            extra["q_from_r"] = {"error": repr(exc)[:300]}
+        torch.cuda.empty_cache()
     if args.batched:
         try:
             extra["batched"] = run_batched(q, lib, torch, dev, stream)
@@ -495,6 +500,33 @@ def run_scholqr3(q, lib, torch, dev, stream, reps=3):
                              "status": inf3.tolist(), "cholqr2_status": infc.tolist(),
                              "rel_diff_vs_tsqr": diff, "tolerance_1e-13_n_kappa": 1e-13 * n * 1e8})
         del X, Xt, ws
+        torch.cuda.empty_cache()
+    return out
+
+
+def run_qform(q, lib, torch, dev, stream, reps=3):
+    """Q = X R^{-1} for the sweep's shape (m = 2^25, kappa = 1e4) from TSQR's R: time per call,
+    GB/s over the bytes moved (X read, Q written) and the orthogonality ||Q^T Q - I||_F."""
+    from paper_2603_20889_gb300 import synth
+
+    out = {"workload": "X = G S, m = 2^25, kappa = 1e4, FP64; R from TSQR", "calls": []}
+    for n in (16, 64):
+        X = synth.conditioned_device(M, n, KAPPA, seed=3000 + n, device=dev)
+        Xt = X.T
+        R, _ = q.tsqr_qless(Xt)
+        Q, info = q.q_from_r(Xt, R)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            q.q_from_r(Xt, R, Q, info)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        orth = float(torch.linalg.norm(Q.T @ Q - torch.eye(n, dtype=torch.float64, device=dev)))
+        out["calls"].append({"n": n, "ms": round(ms, 3), "gbs_moved": round(16.0 * M * n / ms / 1e6, 1),
+                             "status": info.tolist(), "orthogonality": orth})
+        del X, Xt, Q
         torch.cuda.empty_cache()
     return out
 

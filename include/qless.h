@@ -162,6 +162,18 @@ ql_status ql_lstsq_qless(int64_t m, int64_t n, const void* A, int64_t lda, const
                          ql_method method, double* x, double* resnorm, double* Rext, int32_t* info, void* ws,
                          size_t ws_bytes, void* stream);
 
+/*
+ * Q reconstruction: Q = X R^{-1}, the orthonormal factor of X = Q R (the explicit Q of
+ * Sec. 1 that block iterative solvers need), for the R returned by any of the Q-less
+ * calls above (n x n upper triangular, FP64, device, ld ldr >= n).  X is m x n of `dtype`
+ * (ldx >= m); Q (device, m x n, ldq >= m) receives Q in the same dtype; X and Q may not
+ * overlap.  One launch, no workspace: every CTA inverts R in FP64 and forms its rows of Q
+ * in double-float, or in FP64 for row tiles outside the double-float exponent range.  A zero
+ * diagonal entry of R sets info = {QL_ERR_NOT_SPD, i} (1-based) and Q = NaN.
+ */
+ql_status ql_q_from_r(int64_t m, int64_t n, const void* X, ql_dtype dtype, int64_t ldx, const double* R,
+                      int64_t ldr, void* Q, int64_t ldq, int32_t* info, void* stream);
+
 /* ------------------------------------------------------------------ batched form */
 
 /* One problem of a batch.  All pointers are device pointers. */

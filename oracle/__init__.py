@@ -34,6 +34,7 @@ def _load():
             "qo_cholesky_upper": [_I64, _DP, _I64, _DP, _I64],
             "qo_cholqr2": [_I64, _I64, _DP, _I64, _DP, _I64, _DP],
             "qo_scholqr3": [_I64, _I64, _DP, _I64, _DP, _I64],
+            "qo_q_from_r": [_I64, _I64, _DP, _I64, _DP, _I64, _DP, _I64],
             "qo_jacobi_eig": [_I64, _DP, _I64, _DP, _DP, _I64],
             "qo_svqb2": [_I64, _I64, _DP, _I64, _DP, _I64, _DP],
             "qo_back_substitution": [_I64, _DP, _I64, _DP, _DP],
@@ -109,6 +110,16 @@ def scholqr3(X):
     R = np.zeros((n, n), order="F")
     info = _load().qo_scholqr3(m, n, _p(X), max(m, 1), _p(R), n)
     return R, info
+
+
+def q_from_r(X, R):
+    """(Q, info): Q = X R^{-1}; info j+1 when R(j, j) = 0."""
+    X = _f64(X)
+    R = _f64(R)
+    m, n = X.shape
+    Q = np.zeros((m, n), order="F")
+    info = _load().qo_q_from_r(m, n, _p(X), max(m, 1), _p(R), n, _p(Q), max(m, 1))
+    return Q, info
 
 
 def jacobi_eig(C):

@@ -20,6 +20,8 @@
  *   qo_cholqr2         Algorithm 1 (Q-less Cholesky-QR2), step by step.
  *   qo_scholqr3        shifted Cholesky-QR3, the ill-conditioned variant Sec. 1 cites, in the
  *                      published form: chol(X^T X + s I), then Cholesky-QR twice.
+ *   qo_q_from_r        Q = X R^{-1}, the orthonormal factor of X = QR (Sec. 1), by row-wise
+ *                      forward substitution.
  *   qo_jacobi_eig      C = U diag(lambda) U^T (the eigendecomposition that SVQB uses in
  *                      place of chol, Sec. 3.1).
  *   qo_svqb2           SVQB applied twice (Sec. 3.1): B = U Lambda^{-1/2}, X B = Q, and the
@@ -182,6 +184,24 @@ int qo_cholqr2(int64_t m, int64_t n, const double* X, int64_t ldx, double* R, in
 done:
   free(C); free(R1); free(R2); free(Y);
   return info;
+}
+
+/*
+ * Q = X R^{-1} for an upper triangular R with nonzero diagonal: row i of Q solves
+ * q R = x_i (forward substitution over the columns).  Returns j+1 when R(j, j) = 0.
+ */
+int qo_q_from_r(int64_t m, int64_t n, const double* X, int64_t ldx, const double* R, int64_t ldr, double* Q,
+                int64_t ldq) {
+  if (m < 0 || n < 1 || ldx < (m > 1 ? m : 1) || ldr < n || ldq < (m > 1 ? m : 1)) return -1;
+  for (int64_t j = 0; j < n; ++j)
+    if (AT(R, ldr, j, j) == 0.0) return (int)(j + 1);
+  for (int64_t i = 0; i < m; ++i)
+    for (int64_t c = 0; c < n; ++c) {
+      acc_t s = AT(X, ldx, i, c);
+      for (int64_t k = 0; k < c; ++k) s -= (acc_t)AT(Q, ldq, i, k) * (acc_t)AT(R, ldr, k, c);
+      AT(Q, ldq, i, c) = (double)(s / (acc_t)AT(R, ldr, c, c));
+    }
+  return 0;
 }
 
 /*

@@ -41,6 +41,7 @@ SIGNATURES = {
     "ql_tsqr_qless_noalloc": (_i32, [_i64, _i64, _vp, _i32, _i64, _dp, _i64, _vp, _vp]),
     "ql_cholqr2_qless": (_i32, [_i64, _i64, _vp, _i32, _i64, _dp, _i64, _vp, _vp, _sz, _vp]),
     "ql_scholqr3_qless": (_i32, [_i64, _i64, _vp, _i32, _i64, _dp, _i64, _vp, _vp, _sz, _vp]),
+    "ql_q_from_r": (_i32, [_i64, _i64, _vp, _i32, _i64, _dp, _i64, _vp, _i64, _vp, _vp]),
     "ql_svqb_qless": (_i32, [_i64, _i64, _vp, _i32, _i64, _dp, _i64, _dp, _f64, _vp, _vp, _sz, _vp]),
     "ql_lstsq_qless": (_i32, [_i64, _i64, _vp, _i64, _vp, _i32, _i32, _dp, _dp, _dp, _vp, _vp, _sz, _vp]),
     "ql_batch_workspace_bytes": (_sz, [_i32, _vp]),
@@ -212,6 +213,21 @@ def scholqr3_qless(X, R=None, info=None, ws=None, stream=None):
                                           info.data_ptr(), ws.data_ptr(), ws.numel(), _stream_ptr(stream))
     _check(st, "ql_scholqr3_qless")
     return R, info
+
+
+def q_from_r(X, R, Q=None, info=None, stream=None):
+    """Q = X R^{-1} in X's dtype (column-major like X).  Returns (Q, info)."""
+    torch = _torch()
+    m, n, ld, dt = _colmajor(X)
+    if R.dtype != torch.float64 or R.shape != (n, n) or (n > 1 and R.stride(0) != 1):
+        raise ValueError("R must be a column-major n x n float64 tensor")
+    Q = Q if Q is not None else torch.empty((n, m), dtype=X.dtype, device=X.device).T
+    info = info if info is not None else torch.zeros(2, dtype=torch.int32, device=X.device)
+    ldq = Q.stride(1) if n > 1 else max(m, 1)
+    st = load_library().ql_q_from_r(m, n, X.data_ptr(), dt, ld, R.data_ptr(), R.stride(1) if n > 1 else n,
+                                    Q.data_ptr(), ldq, info.data_ptr(), _stream_ptr(stream))
+    _check(st, "ql_q_from_r")
+    return Q, info
 
 
 def svqb_qless(X, R=None, Z=None, rank_tol=0.0, info=None, ws=None, stream=None, want_z=False):

@@ -116,6 +116,58 @@ def test_scholqr3_breakdown_reports_pass_and_pivot():
     assert np.all(np.isnan(to_host(R)))
 
 
+def _colmajor_dev(A):
+    return torch.tensor(np.ascontiguousarray(A.T)).cuda().T
+
+
+@pytest.mark.parametrize("m,n,kappa", [
+    (1, 1, 1.0), (1000, 1, 1.0), (4097, 5, 1e2), (30011, 16, 1e4), (20011, 31, 1e4), (12000, 64, 1e3),
+    (300007, 8, 1.0), (70001, 48, 1e6),
+])
+def test_q_from_r_matches_oracle(m, n, kappa):
+    """Q = X R^{-1} element by element against the oracle's forward substitution, and
+    orthonormal to kappa-scaled rounding."""
+    import paper_2603_20889_gb300 as q
+
+    X, R_ref = case(m, n, kappa, m % 977 + n)
+    Q, info = q.q_from_r(to_dev(X), _colmajor_dev(R_ref))
+    assert info_of(info) == [0, 0]
+    Q = to_host(Q)
+    Q_ref, st = oracle.q_from_r(X, R_ref)
+    assert st == 0
+    assert oracle.rel_err(Q, Q_ref) <= oracle.tolerance(n, kappa)
+    if m >= n:
+        assert np.linalg.norm(Q.T @ Q - np.eye(n)) <= 1e-12 * n * kappa
+
+
+def test_q_from_r_fp32_and_range_fallback():
+    """FP32 X gives FP32 Q (to float rounding); X scaled by 2^70 (outside the double-float
+    range, FP64 tiles) with R scaled alike gives the same Q."""
+    import paper_2603_20889_gb300 as q
+
+    X, R_ref = case(40003, 24, 1e3, 3)
+    Q_ref, _ = oracle.q_from_r(X, R_ref)
+    Q32, info = q.q_from_r(to_dev(X.astype(np.float32)), _colmajor_dev(R_ref))
+    assert info_of(info) == [0, 0] and Q32.dtype == torch.float32
+    X32 = X.astype(np.float32).astype(np.float64)
+    Q_ref32, _ = oracle.q_from_r(X32, R_ref)
+    assert oracle.rel_err(to_host(Q32).astype(np.float64), Q_ref32) <= 1e-6
+    Qs, info = q.q_from_r(to_dev(X * 2.0 ** 70), _colmajor_dev(R_ref * 2.0 ** 70))
+    assert info_of(info) == [0, 0]
+    assert oracle.rel_err(to_host(Qs), Q_ref) <= oracle.tolerance(24, 1e3)
+
+
+def test_q_from_r_zero_pivot_reports_and_fills_nan():
+    import paper_2603_20889_gb300 as q
+
+    X, R_ref = case(5000, 6, 1.0, 5)
+    Rz = R_ref.copy()
+    Rz[3, 3] = 0.0
+    Q, info = q.q_from_r(to_dev(X), _colmajor_dev(Rz))
+    assert info_of(info) == [q.QL_ERR_NOT_SPD, 4]
+    assert np.all(np.isnan(to_host(Q)))
+
+
 def test_svqb_z_factor():
     import paper_2603_20889_gb300 as q
 

@@ -274,6 +274,40 @@ def test_scholqr3_breakdown_index_on_rank_deficiency():
     assert info == 1004
 
 
+@pytest.mark.parametrize("kappa", [1.0, 1e4])
+def test_q_from_r_is_orthonormal_and_reconstructs(kappa):
+    """Q = X R^{-1} for the Householder R: Q^T Q = I (to kappa eps) and Q R = X."""
+    n = 10
+    X = synth.conditioned(2500, n, kappa, seed=11)
+    R = oracle.householder_r(X)
+    Q, info = oracle.q_from_r(X, R)
+    assert info == 0
+    assert np.linalg.norm(Q.T @ Q - np.eye(n)) <= 1e-13 * n * kappa
+    assert np.linalg.norm(Q @ R - X) <= 1e-14 * n * np.linalg.norm(X)
+
+
+def test_q_from_r_hadamard_and_single_column():
+    """X = H[:, :n] R0 has Q = H[:, :n] / sqrt(m); a single column gives x / ||x||."""
+    m, n = 4096, 8
+    X, R_exact = synth.hadamard_case(m, n, seed=4)
+    Q, info = oracle.q_from_r(X, R_exact)
+    assert info == 0
+    H = X @ np.linalg.inv(R_exact / np.sqrt(m))  # exactly +-1 entries up to rounding
+    assert np.max(np.abs(np.round(H) - H)) <= 1e-9 and np.all(np.abs(np.round(H)) == 1.0)
+    assert np.max(np.abs(Q - np.round(H) / np.sqrt(m))) <= 1e-15
+    x = synth.gaussian(333, 1, seed=5)
+    q, _ = oracle.q_from_r(x, np.array([[np.linalg.norm(x)]]))
+    assert np.max(np.abs(q[:, 0] - x[:, 0] / np.linalg.norm(x))) <= 1e-16
+
+
+def test_q_from_r_zero_pivot():
+    X = synth.gaussian(50, 3, seed=6)
+    R = np.triu(np.ones((3, 3)))
+    R[1, 1] = 0.0
+    _, info = oracle.q_from_r(X, R)
+    assert info == 2
+
+
 # ---------------------------------------------------------------- least squares
 
 
