@@ -75,7 +75,7 @@ def parse():
     p.add_argument("--no-batched", dest="batched", action="store_false")
     p.add_argument("--no-serving", dest="serving", action="store_false")
     p.add_argument("--no-next", dest="next_rows", action="store_false",
-                   help="skip the shifted Cholesky-QR3 (kappa = 1e8) and Q = X R^-1 measurements")
+                   help="skip the shifted Cholesky-QR3, Q = X R^-1 and two-phase orthogonalisation measurements")
     p.add_argument("--case", default=None,
                    help="METHOD:N:M -- time one call shape alone (profiling aid; prints its own JSON line)")
     return p.parse_args()
@@ -337,6 +337,11 @@ def run_ours(args, rank, world, local_rank):
         except Exception as exc:
             extra["q_from_r"] = {"error": repr(exc)[:300]}
         torch.cuda.empty_cache()
+        try:
+            extra["project_out"] = run_project(q, lib, torch, dev, stream)
+        except Exception as exc:
+            extra["project_out"] = {"error": repr(exc)[:300]}
+        torch.cuda.empty_cache()
     if args.batched:
         try:
             extra["batched"] = run_batched(q, lib, torch, dev, stream)
@@ -527,6 +532,36 @@ def run_qform(q, lib, torch, dev, stream, reps=3):
         out["calls"].append({"n": n, "ms": round(ms, 3), "gbs_moved": round(16.0 * M * n / ms / 1e6, 1),
                              "status": info.tolist(), "orthogonality": orth})
         del X, Xt, Q
+        torch.cuda.empty_cache()
+    return out
+
+
+def run_project(q, lib, torch, dev, stream, reps=3):
+    """Two-phase orthogonalisation of a block X (m = 2^25, n columns) against an orthonormal
+    Y (k columns, Q of a Gaussian block): time per call, GB/s over the bytes moved (two passes
+    read Y and the block twice and write the block twice), ||Y^T W||_F / ||X||_F."""
+    from paper_2603_20889_gb300 import synth
+
+    out = {"workload": "m = 2^25, Y = Q of a Gaussian m x k, X Gaussian m x n, FP64", "calls": []}
+    for k, n in ((16, 16), (32, 32)):
+        G = synth.conditioned_device(M, k, 1.0, seed=4000 + k, device=dev).T
+        R, _ = q.tsqr_qless(G)
+        Y, _ = q.q_from_r(G, R)
+        X = synth.conditioned_device(M, n, 1.0, seed=4100 + n, device=dev).T
+        W, C = q.project_out(Y, X)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            q.project_out(Y, X, W, C)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        orth = float(torch.linalg.norm(Y.T @ W) / torch.linalg.norm(X))
+        moved = 8.0 * M * (2 * k + 2 * n) * 2
+        out["calls"].append({"k": k, "n": n, "ms": round(ms, 3), "gbs_moved": round(moved / ms / 1e6, 1),
+                             "rel_orthogonality": orth})
+        del G, Y, X, W
         torch.cuda.empty_cache()
     return out
 

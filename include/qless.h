@@ -174,6 +174,21 @@ ql_status ql_lstsq_qless(int64_t m, int64_t n, const void* A, int64_t lda, const
 ql_status ql_q_from_r(int64_t m, int64_t n, const void* X, ql_dtype dtype, int64_t ldx, const double* R,
                       int64_t ldr, void* Q, int64_t ldq, int32_t* info, void* stream);
 
+/*
+ * Two-phase orthogonalisation: the "two-phase problem" QR = (I - Y Y^T) X with
+ * re-orthogonalisation that Sec. 2 discusses, for Y (m x k, orthonormal columns, 1 <= k <=
+ * 64, ld ldy) and X (m x n, 1 <= n <= 64, ld ldx), both of `dtype`:
+ *   C1 = Y^T X,  W1 = X - Y C1,  C2 = Y^T W1,  W = W1 - Y C2,
+ * W (device, m x n of dtype, ld ldw; may be X itself) receives the projected block and C
+ * (device double k x n, ld ldc >= k) the coefficients C1 + C2, so X = Y C + W.  The R of the
+ * orthogonalised block is any Q-less call on W.  Four launches; the Y^T V products are
+ * reduced in a fixed order (reproducible).  ws: ql_project_workspace_bytes(k, n) bytes.
+ */
+size_t ql_project_workspace_bytes(int64_t k, int64_t n);
+ql_status ql_project_out(int64_t m, int64_t k, const void* Y, int64_t ldy, int64_t n, const void* X, int64_t ldx,
+                         ql_dtype dtype, void* W, int64_t ldw, double* C, int64_t ldc, void* ws, size_t ws_bytes,
+                         void* stream);
+
 /* ------------------------------------------------------------------ batched form */
 
 /* One problem of a batch.  All pointers are device pointers. */

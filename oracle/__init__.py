@@ -35,6 +35,7 @@ def _load():
             "qo_cholqr2": [_I64, _I64, _DP, _I64, _DP, _I64, _DP],
             "qo_scholqr3": [_I64, _I64, _DP, _I64, _DP, _I64],
             "qo_q_from_r": [_I64, _I64, _DP, _I64, _DP, _I64, _DP, _I64],
+            "qo_project_out": [_I64, _I64, _DP, _I64, _I64, _DP, _I64, _DP, _I64, _DP, _I64],
             "qo_jacobi_eig": [_I64, _DP, _I64, _DP, _DP, _I64],
             "qo_svqb2": [_I64, _I64, _DP, _I64, _DP, _I64, _DP],
             "qo_back_substitution": [_I64, _DP, _I64, _DP, _DP],
@@ -120,6 +121,20 @@ def q_from_r(X, R):
     Q = np.zeros((m, n), order="F")
     info = _load().qo_q_from_r(m, n, _p(X), max(m, 1), _p(R), n, _p(Q), max(m, 1))
     return Q, info
+
+
+def project_out(Y, X):
+    """(W, C): two projections of X against orthonormal Y, X = Y C + W."""
+    Y = _f64(Y)
+    X = _f64(X)
+    m, k = Y.shape
+    n = X.shape[1]
+    W = np.zeros((m, n), order="F")
+    C = np.zeros((k, n), order="F")
+    info = _load().qo_project_out(m, k, _p(Y), max(m, 1), n, _p(X), max(m, 1), _p(W), max(m, 1), _p(C), k)
+    if info:
+        raise OracleError(f"qo_project_out info={info}")
+    return W, C
 
 
 def jacobi_eig(C):

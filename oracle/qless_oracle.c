@@ -22,6 +22,8 @@
  *                      published form: chol(X^T X + s I), then Cholesky-QR twice.
  *   qo_q_from_r        Q = X R^{-1}, the orthonormal factor of X = QR (Sec. 1), by row-wise
  *                      forward substitution.
+ *   qo_project_out     the two-phase problem (I - Y Y^T) X with re-orthogonalisation (Sec. 2):
+ *                      two projection passes, coefficients accumulated.
  *   qo_jacobi_eig      C = U diag(lambda) U^T (the eigendecomposition that SVQB uses in
  *                      place of chol, Sec. 3.1).
  *   qo_svqb2           SVQB applied twice (Sec. 3.1): B = U Lambda^{-1/2}, X B = Q, and the
@@ -202,6 +204,45 @@ int qo_q_from_r(int64_t m, int64_t n, const double* X, int64_t ldx, const double
       AT(Q, ldq, i, c) = (double)(s / (acc_t)AT(R, ldr, c, c));
     }
   return 0;
+}
+
+/*
+ * Two projections against Y (m x k, orthonormal columns):  C1 = Y^T X;  W1 = X - Y C1;
+ * C2 = Y^T W1;  W = W1 - Y C2;  C = C1 + C2 (k x n, ld ldc).  W (m x n, ld ldw).
+ */
+static void project_once(int64_t m, int64_t k, const double* Y, int64_t ldy, int64_t n, const double* V,
+                         int64_t ldv, double* Cp, double* W, int64_t ldw) {
+  for (int64_t j = 0; j < n; ++j)
+    for (int64_t i = 0; i < k; ++i) {
+      acc_t s = 0.0L;
+      for (int64_t r = 0; r < m; ++r) s += (acc_t)AT(Y, ldy, r, i) * (acc_t)AT(V, ldv, r, j);
+      AT(Cp, k, i, j) = (double)s;
+    }
+  for (int64_t j = 0; j < n; ++j)
+    for (int64_t r = 0; r < m; ++r) {
+      acc_t w = AT(V, ldv, r, j);
+      for (int64_t i = 0; i < k; ++i) w -= (acc_t)AT(Y, ldy, r, i) * (acc_t)AT(Cp, k, i, j);
+      AT(W, ldw, r, j) = (double)w;
+    }
+}
+
+int qo_project_out(int64_t m, int64_t k, const double* Y, int64_t ldy, int64_t n, const double* X, int64_t ldx,
+                   double* W, int64_t ldw, double* C, int64_t ldc) {
+  int64_t lmin = m > 1 ? m : 1;
+  if (m < 0 || k < 1 || n < 1 || ldy < lmin || ldx < lmin || ldw < lmin || ldc < k) return -1;
+  double* C1 = (double*)malloc((size_t)k * (size_t)n * sizeof(double));
+  double* C2 = (double*)malloc((size_t)k * (size_t)n * sizeof(double));
+  double* W1 = (double*)malloc((size_t)lmin * (size_t)n * sizeof(double));
+  int info = -1;
+  if (!C1 || !C2 || !W1) goto done;
+  project_once(m, k, Y, ldy, n, X, ldx, C1, W1, lmin);
+  project_once(m, k, Y, ldy, n, W1, lmin, C2, W, ldw);
+  for (int64_t j = 0; j < n; ++j)
+    for (int64_t i = 0; i < k; ++i) AT(C, ldc, i, j) = AT(C1, k, i, j) + AT(C2, k, i, j);
+  info = 0;
+done:
+  free(C1); free(C2); free(W1);
+  return info;
 }
 
 /*

@@ -42,6 +42,8 @@ SIGNATURES = {
     "ql_cholqr2_qless": (_i32, [_i64, _i64, _vp, _i32, _i64, _dp, _i64, _vp, _vp, _sz, _vp]),
     "ql_scholqr3_qless": (_i32, [_i64, _i64, _vp, _i32, _i64, _dp, _i64, _vp, _vp, _sz, _vp]),
     "ql_q_from_r": (_i32, [_i64, _i64, _vp, _i32, _i64, _dp, _i64, _vp, _i64, _vp, _vp]),
+    "ql_project_workspace_bytes": (_sz, [_i64, _i64]),
+    "ql_project_out": (_i32, [_i64, _i64, _vp, _i64, _i64, _vp, _i64, _i32, _vp, _i64, _dp, _i64, _vp, _sz, _vp]),
     "ql_svqb_qless": (_i32, [_i64, _i64, _vp, _i32, _i64, _dp, _i64, _dp, _f64, _vp, _vp, _sz, _vp]),
     "ql_lstsq_qless": (_i32, [_i64, _i64, _vp, _i64, _vp, _i32, _i32, _dp, _dp, _dp, _vp, _vp, _sz, _vp]),
     "ql_batch_workspace_bytes": (_sz, [_i32, _vp]),
@@ -228,6 +230,29 @@ def q_from_r(X, R, Q=None, info=None, stream=None):
                                     Q.data_ptr(), ldq, info.data_ptr(), _stream_ptr(stream))
     _check(st, "ql_q_from_r")
     return Q, info
+
+
+def project_out(Y, X, W=None, C=None, ws=None, stream=None):
+    """Two-phase orthogonalisation against orthonormal Y: W = (I - Y Y^T) X (projected twice),
+    C = Y^T X accumulated over both passes (X = Y C + W).  Returns (W, C)."""
+    torch = _torch()
+    m, k, ldy, dty = _colmajor(Y)
+    m2, n, ldx, dt = _colmajor(X)
+    if m2 != m or dty != dt:
+        raise ValueError("Y and X need the same rows and dtype")
+    W = W if W is not None else torch.empty((n, m), dtype=X.dtype, device=X.device).T
+    C = C if C is not None else torch.empty((n, k), dtype=torch.float64, device=X.device).T
+    lib = load_library()
+    if ws is None:
+        nb = lib.ql_project_workspace_bytes(k, n)
+        if nb == 0:
+            raise QlError(QL_ERR_ARG, "ql_project_workspace_bytes")
+        ws = torch.empty(nb, dtype=torch.uint8, device=X.device)
+    ldw = W.stride(1) if n > 1 else max(m, 1)
+    st = lib.ql_project_out(m, k, Y.data_ptr(), ldy, n, X.data_ptr(), ldx, dt, W.data_ptr(), ldw, C.data_ptr(),
+                            C.stride(1) if n > 1 else k, ws.data_ptr(), ws.numel(), _stream_ptr(stream))
+    _check(st, "ql_project_out")
+    return W, C
 
 
 def svqb_qless(X, R=None, Z=None, rank_tol=0.0, info=None, ws=None, stream=None, want_z=False):

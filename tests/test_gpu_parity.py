@@ -168,6 +168,53 @@ def test_q_from_r_zero_pivot_reports_and_fills_nan():
     assert np.all(np.isnan(to_host(Q)))
 
 
+def _orthonormal_basis(m, k, seed):
+    Y = synth.gaussian(m, k, seed=seed)
+    Q, info = oracle.q_from_r(Y, oracle.householder_r(Y))
+    assert info == 0
+    return Q
+
+
+@pytest.mark.parametrize("m,k,n", [(1, 1, 1), (1000, 3, 5), (30011, 16, 16), (20011, 31, 9), (12000, 64, 64),
+                                   (100003, 8, 40)])
+def test_project_out_matches_oracle(m, k, n):
+    """Two-phase orthogonalisation: W and C element by element against the oracle, W
+    orthogonal to Y and X = Y C + W."""
+    import paper_2603_20889_gb300 as q
+
+    Y = _orthonormal_basis(m, k, 31 + k) if m >= k else synth.gaussian(m, k, seed=3)
+    X = synth.gaussian(m, n, seed=32 + n) + Y @ synth.gaussian(k, n, seed=33)  # largely in range(Y)
+    W_ref, C_ref = oracle.project_out(Y, X)
+    W, C = q.project_out(to_dev(Y), to_dev(X))
+    W, C = to_host(W), to_host(C)
+    scale = np.linalg.norm(X)
+    assert np.linalg.norm(W - W_ref) <= 1e-13 * (k + n) * scale
+    assert np.linalg.norm(C - C_ref) <= 1e-13 * (k + n) * scale
+    if m >= k:
+        assert np.linalg.norm(Y.T @ W) <= 1e-13 * (k + n) * scale
+    assert np.linalg.norm(Y @ C + W - X) <= 1e-13 * (k + n) * scale
+
+
+def test_project_out_fp32_inplace_and_exact_orthogonal_case():
+    """FP32 storage (W to float rounding), W written over X, and Hadamard columns exactly
+    orthogonal to Y giving C = 0 and W = X bitwise."""
+    import paper_2603_20889_gb300 as q
+
+    m, k, n = 40000, 12, 10
+    Y = _orthonormal_basis(m, k, 41)
+    X = synth.gaussian(m, n, seed=42)
+    W_ref, C_ref = oracle.project_out(Y.astype(np.float32).astype(np.float64), X.astype(np.float32).astype(np.float64))
+    Xd = to_dev(X.astype(np.float32))
+    W, C = q.project_out(to_dev(Y.astype(np.float32)), Xd, W=Xd)  # in place
+    assert W.data_ptr() == Xd.data_ptr()
+    assert np.linalg.norm(to_host(W).astype(np.float64) - W_ref) <= 1e-6 * np.linalg.norm(X)
+    assert np.linalg.norm(to_host(C) - C_ref) <= 1e-6 * np.linalg.norm(X)
+    H = synth.hadamard_columns(65536, 24)
+    Yh, Xh = H[:, :8] / 256.0, H[:, 8:]
+    W, C = q.project_out(to_dev(Yh), to_dev(Xh))
+    assert np.all(to_host(C) == 0.0) and np.array_equal(to_host(W), Xh)
+
+
 def test_svqb_z_factor():
     import paper_2603_20889_gb300 as q
 

@@ -308,6 +308,38 @@ def test_q_from_r_zero_pivot():
     assert info == 2
 
 
+def _orthonormal(m, k, seed):
+    Y = synth.gaussian(m, k, seed=seed)
+    Q, info = oracle.q_from_r(Y, oracle.householder_r(Y))
+    assert info == 0
+    return Q
+
+
+def test_project_out_orthogonal_and_reconstructs():
+    """Two projections leave W orthogonal to Y to rounding, and X = Y C + W."""
+    m, k, n = 3000, 6, 5
+    Y = _orthonormal(m, k, 21)
+    X = synth.gaussian(m, n, seed=22)
+    W, C = oracle.project_out(Y, X)
+    assert np.linalg.norm(Y.T @ W) <= 1e-14 * np.linalg.norm(X)
+    assert np.linalg.norm(Y @ C + W - X) <= 1e-14 * np.linalg.norm(X)
+    assert np.linalg.norm(C - Y.T @ X) <= 1e-13 * np.linalg.norm(X)
+
+
+def test_project_out_in_range_and_exactly_orthogonal():
+    """X = Y B gives W ~ 0 and C ~ B; Hadamard columns orthogonal to Y give C = 0, W = X exactly."""
+    m, k = 2000, 4
+    Y = _orthonormal(m, k, 23)
+    B = synth.gaussian(k, 3, seed=24)
+    W, C = oracle.project_out(Y, Y @ B)
+    assert np.linalg.norm(W) <= 1e-14 * np.linalg.norm(B)
+    assert np.linalg.norm(C - B) <= 1e-14 * np.linalg.norm(B)
+    H = synth.hadamard_columns(1024, 9)
+    Yh, Xh = H[:, :4] / 32.0, H[:, 4:]
+    Wh, Ch = oracle.project_out(Yh, Xh)
+    assert np.all(Ch == 0.0) and np.array_equal(Wh, Xh)
+
+
 # ---------------------------------------------------------------- least squares
 
 
