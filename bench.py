@@ -75,7 +75,8 @@ def parse():
     p.add_argument("--no-batched", dest="batched", action="store_false")
     p.add_argument("--no-serving", dest="serving", action="store_false")
     p.add_argument("--no-next", dest="next_rows", action="store_false",
-                   help="skip the shifted Cholesky-QR3, Q = X R^-1 and two-phase orthogonalisation measurements")
+                   help="skip the measurements of the rows beyond the sweep (shifted Cholesky-QR3, Q = X R^-1, "
+                        "two-phase orthogonalisation, n > 64)")
     p.add_argument("--case", default=None,
                    help="METHOD:N:M -- time one call shape alone (profiling aid; prints its own JSON line)")
     return p.parse_args()
@@ -342,6 +343,11 @@ def run_ours(args, rank, world, local_rank):
         except Exception as exc:
             extra["project_out"] = {"error": repr(exc)[:300]}
         torch.cuda.empty_cache()
+        try:
+            extra["qr_wide"] = run_wide(q, lib, torch, dev, stream)
+        except Exception as exc:
+            extra["qr_wide"] = {"error": repr(exc)[:300]}
+        torch.cuda.empty_cache()
     if args.batched:
         try:
             extra["batched"] = run_batched(q, lib, torch, dev, stream)
@@ -562,6 +568,35 @@ def run_project(q, lib, torch, dev, stream, reps=3):
         out["calls"].append({"k": k, "n": n, "ms": round(ms, 3), "gbs_moved": round(moved / ms / 1e6, 1),
                              "rel_orthogonality": orth})
         del G, Y, X, W
+        torch.cuda.empty_cache()
+    return out
+
+
+def run_wide(q, lib, torch, dev, stream, reps=2):
+    """QR of wider X (m = 2^22, n = 128 and 256, kappa = 1e3, FP64) by 64-column panels:
+    time per call, effective GB/s (8 m n bytes), ||Q^T Q - I||_F and the R difference from
+    a one-panel check (TSQR R of the first 64 columns)."""
+    from paper_2603_20889_gb300 import synth
+
+    m = 1 << 22
+    out = {"workload": "X = G S, m = 2^22, kappa = 1e3, FP64", "calls": []}
+    for n in (128, 256):
+        X = synth.conditioned_device(m, n, 1e3, seed=5000 + n, device=dev).T
+        Q, R, info = q.qr_wide(X)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            q.qr_wide(X, R, Q, info)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        orth = float(torch.linalg.norm(Q.T @ Q - torch.eye(n, dtype=torch.float64, device=dev)))
+        R1, _ = q.tsqr_qless(X[:, :64].contiguous().T.contiguous().T)
+        d1 = float(torch.linalg.norm(R[:64, :64] - R1) / torch.linalg.norm(R1))
+        out["calls"].append({"n": n, "ms": round(ms, 3), "eff_gbs": round(8.0 * m * n / ms / 1e6, 1),
+                             "status": info.tolist(), "orthogonality": orth, "first_panel_vs_tsqr": d1})
+        del X, Q, R
         torch.cuda.empty_cache()
     return out
 

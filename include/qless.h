@@ -189,6 +189,20 @@ ql_status ql_project_out(int64_t m, int64_t k, const void* Y, int64_t ldy, int64
                          ql_dtype dtype, void* W, int64_t ldw, double* C, int64_t ldc, void* ws, size_t ws_bytes,
                          void* stream);
 
+/*
+ * QR of wider matrices (65 <= n <= 4096; any n >= 1 works): the hybrid of block
+ * Gram-Schmidt and TSQR panels that the paper's outlook names beyond the very-skinny
+ * regime.  Panels of 64 columns, left to right: each is projected twice against all earlier
+ * panels' Q (ql_project_out; the coefficients are R's off-diagonal blocks), factored by TSQR
+ * (R's diagonal block) and turned into its Q by ql_q_from_r.  R (device double n x n, ld
+ * ldr, lower triangle zeroed); Q (device m x n of dtype, ld ldq) receives the orthonormal
+ * factor; info (nullable) the first failing call's {status, index}.  No allocation:
+ * ws of ql_qr_wide_workspace_bytes(m, n, dtype) bytes.  Every step runs on `stream`.
+ */
+size_t ql_qr_wide_workspace_bytes(int64_t m, int64_t n, ql_dtype dtype);
+ql_status ql_qr_wide(int64_t m, int64_t n, const void* X, ql_dtype dtype, int64_t ldx, double* R, int64_t ldr,
+                     void* Q, int64_t ldq, int32_t* info, void* ws, size_t ws_bytes, void* stream);
+
 /* ------------------------------------------------------------------ batched form */
 
 /* One problem of a batch.  All pointers are device pointers. */

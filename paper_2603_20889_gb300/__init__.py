@@ -43,6 +43,8 @@ SIGNATURES = {
     "ql_scholqr3_qless": (_i32, [_i64, _i64, _vp, _i32, _i64, _dp, _i64, _vp, _vp, _sz, _vp]),
     "ql_q_from_r": (_i32, [_i64, _i64, _vp, _i32, _i64, _dp, _i64, _vp, _i64, _vp, _vp]),
     "ql_project_workspace_bytes": (_sz, [_i64, _i64]),
+    "ql_qr_wide_workspace_bytes": (_sz, [_i64, _i64, _i32]),
+    "ql_qr_wide": (_i32, [_i64, _i64, _vp, _i32, _i64, _dp, _i64, _vp, _i64, _vp, _vp, _sz, _vp]),
     "ql_project_out": (_i32, [_i64, _i64, _vp, _i64, _i64, _vp, _i64, _i32, _vp, _i64, _dp, _i64, _vp, _sz, _vp]),
     "ql_svqb_qless": (_i32, [_i64, _i64, _vp, _i32, _i64, _dp, _i64, _dp, _f64, _vp, _vp, _sz, _vp]),
     "ql_lstsq_qless": (_i32, [_i64, _i64, _vp, _i64, _vp, _i32, _i32, _dp, _dp, _dp, _vp, _vp, _sz, _vp]),
@@ -253,6 +255,26 @@ def project_out(Y, X, W=None, C=None, ws=None, stream=None):
                             C.stride(1) if n > 1 else k, ws.data_ptr(), ws.numel(), _stream_ptr(stream))
     _check(st, "ql_project_out")
     return W, C
+
+
+def qr_wide(X, R=None, Q=None, info=None, ws=None, stream=None):
+    """QR of an m x n matrix with any n (64-column panels): returns (Q, R, info)."""
+    torch = _torch()
+    m, n, ld, dt = _colmajor(X)
+    R = R if R is not None else torch.empty((n, n), dtype=torch.float64, device=X.device).T
+    Q = Q if Q is not None else torch.empty((n, m), dtype=X.dtype, device=X.device).T
+    info = info if info is not None else torch.zeros(2, dtype=torch.int32, device=X.device)
+    lib = load_library()
+    if ws is None:
+        nb = lib.ql_qr_wide_workspace_bytes(m, n, dt)
+        if nb == 0:
+            raise QlError(QL_ERR_ARG, "ql_qr_wide_workspace_bytes")
+        ws = torch.empty(nb, dtype=torch.uint8, device=X.device)
+    st = lib.ql_qr_wide(m, n, X.data_ptr(), dt, ld, R.data_ptr(), R.stride(1) if n > 1 else n, Q.data_ptr(),
+                        Q.stride(1) if n > 1 else max(m, 1), info.data_ptr(), ws.data_ptr(), ws.numel(),
+                        _stream_ptr(stream))
+    _check(st, "ql_qr_wide")
+    return Q, R, info
 
 
 def svqb_qless(X, R=None, Z=None, rank_tol=0.0, info=None, ws=None, stream=None, want_z=False):

@@ -78,6 +78,8 @@ int tsqr_variant();
 
 // Counts every kernel this library launches (reported by ql_launch_count()).
 void count_launch();
+// dst = the first nonzero {status, index} pair among src[0 .. count) (one tiny launch).
+ql_status first_status_async(int32_t* dst, const int32_t* src, int count, cudaStream_t stream);
 
 // Autotune table lookup (method, CTAs per SM) for an (m, n, dtype, kappa) class.
 bool tune_lookup(int64_t m, int64_t n, ql_dtype dt, double kappa, int* method, int* ctas);

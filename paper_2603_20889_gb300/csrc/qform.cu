@@ -209,6 +209,26 @@ static ql_status qform_dispatch(QformArgs<S> a, cudaStream_t stream) {
   return qform_launch_one<64, S>(a, stream);
 }
 
+// dst <- the first nonzero {status, index} pair of src[0 .. count) (or {QL_OK, 0})
+__global__ void first_status_kernel(int32_t* dst, const int32_t* src, int count) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int32_t s = 0, i = 0;
+  for (int c = 0; c < count; ++c)
+    if (src[2 * c] != 0) {
+      s = src[2 * c];
+      i = src[2 * c + 1];
+      break;
+    }
+  dst[0] = s;
+  dst[1] = i;
+}
+
+ql_status first_status_async(int32_t* dst, const int32_t* src, int count, cudaStream_t stream) {
+  count_launch();
+  first_status_kernel<<<1, 32, 0, stream>>>(dst, src, count);
+  return cudaPeekAtLastError() == cudaSuccess ? QL_OK : QL_ERR_CUDA;
+}
+
 }  // namespace ql
 
 using namespace ql;

@@ -215,6 +215,29 @@ def test_project_out_fp32_inplace_and_exact_orthogonal_case():
     assert np.all(to_host(C) == 0.0) and np.array_equal(to_host(W), Xh)
 
 
+@pytest.mark.parametrize("m,n,kappa,dtype", [
+    (5000, 65, 1e2, "f64"), (20011, 100, 1e3, "f64"), (30000, 130, 1e2, "f64"), (8000, 200, 10.0, "f64"),
+    (12000, 40, 1e3, "f64"), (20000, 96, 1e2, "f32"),
+])
+def test_qr_wide_matches_oracle(m, n, kappa, dtype):
+    """n > 64 by 64-column panels (block Gram-Schmidt with two-phase projections + TSQR):
+    R against the oracle's Householder R, Q orthonormal, Q R = X."""
+    import paper_2603_20889_gb300 as q
+
+    X, R_ref = case(m, n, kappa, m % 983 + n)
+    Xs = X.astype(np.float32) if dtype == "f32" else X
+    if dtype == "f32":
+        R_ref = oracle.householder_r(Xs.astype(np.float64))
+    Q, R, info = q.qr_wide(to_dev(Xs))
+    assert info_of(info) == [0, 0]
+    Q, R = to_host(Q).astype(np.float64), to_host(R)
+    assert np.all(np.tril(R, -1) == 0.0) and np.all(np.diag(R) > 0.0)
+    assert oracle.rel_err(R, R_ref) <= (oracle.tolerance(n, kappa) if dtype == "f64" else 1e-5)
+    orth = 1e-12 * n * kappa if dtype == "f64" else 1e-4
+    assert np.linalg.norm(Q.T @ Q - np.eye(n)) <= orth
+    assert np.linalg.norm(Q @ R - Xs.astype(np.float64)) <= (1e-13 if dtype == "f64" else 1e-5) * n * np.linalg.norm(X)
+
+
 def test_svqb_z_factor():
     import paper_2603_20889_gb300 as q
 
