@@ -754,16 +754,24 @@ ql_status gram_tc_launch_one(const GramCall& c, const GramWs& w, int pass) {
 // Tensor-core Gram pass on tcgen05 (double-float policy only): see gram_umma.cuh.  The
 // second pass forms Y = X M' with mma.sync as in gram_tc_kernel (B fragments of M' in
 // registers), reading X's digit planes in the core-matrix layout.
+// Block size: 512 threads for the first pass (latency-bound slicing and TMEM read-out gain
+// from 16 warps), 256 for the later passes (their M' fragments need the registers).
+template <int XF>
+__host__ __device__ constexpr int umma_threads() {
+  return XF == kXNone ? 512 : 256;
+}
+
 template <int NC, typename S, int XF>
-__global__ void __launch_bounds__(256, 1) gram_umma_kernel(GramArgs<S> a) {
+__global__ void __launch_bounds__(umma_threads<XF>(), 1) gram_umma_kernel(GramArgs<S> a) {
   using Sh = UmmaShape<NC>;
   using Sm = UmmaSmem<NC, S>;
-  constexpr int T = 256, KT = Sh::KT, LDS = Sm::LDS, LDY = Sm::LDY, SP = Sh::SP, PLANE = Sh::PLANE;
+  constexpr int T = umma_threads<XF>(), NW = T / 32, KT = Sh::KT, LDS = Sm::LDS, LDY = Sm::LDY, SP = Sh::SP,
+                PLANE = Sh::PLANE;
   constexpr int SBO = Sh::SBO, LBO = Sh::LBO;
   constexpr int PAIRS = NC * KT / 2 / T;        // row pairs (and core-matrix quarters) per thread and tile
   constexpr int KSTEPS = NC / 16;               // 16-wide k-steps of Y = X M'
   constexpr int WPC = 8 / (NC / 8);             // warps per 8-column block of Y
-  constexpr int HALF = NC / 2;                  // accumulator columns per thread
+  constexpr int HALF = NC / (NW / 4);           // accumulator columns per thread (NW / 4 warps per lane quarter)
   constexpr int CPG = KT / 8;                   // core matrices per 8-column group
   constexpr uint32_t IDESC = umma_idesc_bf16(128, NC);
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -864,7 +872,7 @@ __global__ void __launch_bounds__(256, 1) gram_umma_kernel(GramArgs<S> a) {
   tc_fence_after();
   const uint32_t tbase = *tslot;
 
-  const int qd = warp & 3, hh = warp >> 2;  // TMEM lane quarter and column half of this warp
+  const int qd = warp & 3, hh = warp >> 2;  // TMEM lane quarter and column part of this warp
   const int L = 32 * qd + lane, kq = L / NC, li = L % NC;
   df acc[HALF];
 #pragma unroll
@@ -924,7 +932,7 @@ __global__ void __launch_bounds__(256, 1) gram_umma_kernel(GramArgs<S> a) {
   auto slice_stage = [&](const int* ex) {
 #pragma unroll 4
     for (int k2 = 0; k2 < PAIRS; ++k2) {
-      const int cm = warp + 8 * k2, c = 8 * (cm / CPG) + (lane >> 2), r = 8 * (cm % CPG) + 2 * (lane & 3);
+      const int cm = warp + NW * k2, c = 8 * (cm / CPG) + (lane >> 2), r = 8 * (cm % CPG) + 2 * (lane & 3);
       const int em = c < n ? ex[c] : 0;  // columns past n are zero (a bulk-loaded stage holds stale data there)
       unsigned long long N[2];
       unsigned sg[2];
@@ -1046,7 +1054,7 @@ __global__ void __launch_bounds__(256, 1) gram_umma_kernel(GramArgs<S> a) {
       // slicing of Y at its per-tile column scale
 #pragma unroll 4
       for (int k2 = 0; k2 < PAIRS; ++k2) {
-        const int cm = warp + 8 * k2, c = 8 * (cm / CPG) + (lane >> 2), r = 8 * (cm % CPG) + 2 * (lane & 3);
+        const int cm = warp + NW * k2, c = 8 * (cm / CPG) + (lane >> 2), r = 8 * (cm % CPG) + 2 * (lane & 3);
         const int em = expo[c];
         unsigned long long N[2];
         unsigned sg[2];
@@ -1206,7 +1214,7 @@ ql_status gram_umma_launch_one(const GramCall& c, const GramWs& w, int pass) {
     a.bulk = b ? 1 : 0;
   }
   count_launch();
-  kern<<<(int)g, Sh::T, Sm::kBytes, c.stream>>>(a);
+  kern<<<(int)g, umma_threads<XF>(), Sm::kBytes, c.stream>>>(a);
   return cudaPeekAtLastError() == cudaSuccess ? QL_OK : QL_ERR_CUDA;
 }
 
@@ -1267,13 +1275,15 @@ ql_status gram_dispatch(const GramCall& c, const GramWs& w, int gated) {
       if (tc_gram_enabled()) {
         // tcgen05 for 64 columns; below that, stacking 128 / NC planes spreads every weight
         // over 4 or 8 lane groups and the TMEM read-out costs more than mma.sync saves
-        if (NC == 64 && umma_gram_enabled()) {
-          ql_status st = gram_umma_launch_one<NC, S, kXNone>(c, w, 1);
-          if (st) return st;
-          if (c.method == QL_SVQB2) return gram_umma_launch_one<NC, S, kXFull>(c, w, 2);
-          st = gram_umma_launch_one<NC, S, kXUpper>(c, w, 2);
-          if (st || c.method != QL_SCHOLQR3) return st;
-          return gram_umma_launch_one<NC, S, kXUpper>(c, w, 3);
+        if constexpr (NC == 64) {
+          if (umma_gram_enabled()) {
+            ql_status st = gram_umma_launch_one<NC, S, kXNone>(c, w, 1);
+            if (st) return st;
+            if (c.method == QL_SVQB2) return gram_umma_launch_one<NC, S, kXFull>(c, w, 2);
+            st = gram_umma_launch_one<NC, S, kXUpper>(c, w, 2);
+            if (st || c.method != QL_SCHOLQR3) return st;
+            return gram_umma_launch_one<NC, S, kXUpper>(c, w, 3);
+          }
         }
         ql_status st = gram_tc_launch_one<NC, S, kXNone>(c, w, 1);
         if (st) return st;
