@@ -15,14 +15,6 @@ bool tc_gram_enabled() {
   return on;
 }
 
-bool umma_gram_enabled() {
-  static const bool on = [] {
-    const char* v = std::getenv("QL_GRAM_MMA_SYNC");
-    return !(v && v[0] == '1');
-  }();
-  return on;
-}
-
 static int nc_of(int n) { return n <= 1 ? 1 : n <= 2 ? 2 : n <= 4 ? 4 : n <= 8 ? 8 : n <= 16 ? 16 : n <= 32 ? 32 : 64; }
 
 static size_t gram_layout(int n, GramWs* w, void* base) {

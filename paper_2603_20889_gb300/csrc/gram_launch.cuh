@@ -1273,24 +1273,23 @@ ql_status gram_dispatch(const GramCall& c, const GramWs& w, int gated) {
     constexpr int NC = decltype(nc_tag)::value;
     if constexpr (NC >= 16 && std::is_same<Ar, ArithDF>::value) {
       if (tc_gram_enabled()) {
-        // tcgen05 for 64 columns; below that, stacking 128 / NC planes spreads every weight
-        // over 4 or 8 lane groups and the TMEM read-out costs more than mma.sync saves
+        // tcgen05 for 64 columns; below that, stacking 128 / NC planes would spread every
+        // weight over 4 or 8 lane groups and the TMEM read-out cost more than mma.sync saves
         if constexpr (NC == 64) {
-          if (umma_gram_enabled()) {
-            ql_status st = gram_umma_launch_one<NC, S, kXNone>(c, w, 1);
-            if (st) return st;
-            if (c.method == QL_SVQB2) return gram_umma_launch_one<NC, S, kXFull>(c, w, 2);
-            st = gram_umma_launch_one<NC, S, kXUpper>(c, w, 2);
-            if (st || c.method != QL_SCHOLQR3) return st;
-            return gram_umma_launch_one<NC, S, kXUpper>(c, w, 3);
-          }
+          ql_status st = gram_umma_launch_one<NC, S, kXNone>(c, w, 1);
+          if (st) return st;
+          if (c.method == QL_SVQB2) return gram_umma_launch_one<NC, S, kXFull>(c, w, 2);
+          st = gram_umma_launch_one<NC, S, kXUpper>(c, w, 2);
+          if (st || c.method != QL_SCHOLQR3) return st;
+          return gram_umma_launch_one<NC, S, kXUpper>(c, w, 3);
+        } else {
+          ql_status st = gram_tc_launch_one<NC, S, kXNone>(c, w, 1);
+          if (st) return st;
+          if (c.method == QL_SVQB2) return gram_tc_launch_one<NC, S, kXFull>(c, w, 2);
+          st = gram_tc_launch_one<NC, S, kXUpper>(c, w, 2);
+          if (st || c.method != QL_SCHOLQR3) return st;
+          return gram_tc_launch_one<NC, S, kXUpper>(c, w, 3);
         }
-        ql_status st = gram_tc_launch_one<NC, S, kXNone>(c, w, 1);
-        if (st) return st;
-        if (c.method == QL_SVQB2) return gram_tc_launch_one<NC, S, kXFull>(c, w, 2);
-        st = gram_tc_launch_one<NC, S, kXUpper>(c, w, 2);
-        if (st || c.method != QL_SCHOLQR3) return st;
-        return gram_tc_launch_one<NC, S, kXUpper>(c, w, 3);
       }
     }
     ql_status st = gram_launch_one<NC, S, Ar, kXNone>(c, w, 1, gated);

@@ -68,10 +68,9 @@ ql_status gram_launch(const GramCall& c, ql_arith arith);
 
 int device_sm_count();
 ql_arith current_arith();
-// Whether the Gram passes use the tensor-core kernels (double-float mode, n >= 5);
+// Whether the Gram passes use the tensor-core kernels (double-float mode, n >= 9);
 // the environment variable QL_GRAM_SIMT=1 selects the SIMT kernels instead.
 bool tc_gram_enabled();
-bool umma_gram_enabled();
 
 // Thread-layout variant of the TSQR kernels (environment QL_TSQR_CFG, 0 = default).
 int tsqr_variant();
