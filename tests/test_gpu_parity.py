@@ -238,6 +238,23 @@ def test_qr_wide_matches_oracle(m, n, kappa, dtype):
     assert np.linalg.norm(Q @ R - Xs.astype(np.float64)) <= (1e-13 if dtype == "f64" else 1e-5) * n * np.linalg.norm(X)
 
 
+def test_extension_entry_points_on_empty_and_single_column_inputs():
+    """m = 0 and n = 1 through Q = X R^-1, the two-phase projection and the wide QR."""
+    import paper_2603_20889_gb300 as q
+
+    X0 = torch.zeros((3, 0), dtype=torch.float64, device="cuda").T  # 0 x 3, column-major
+    R = _colmajor_dev(np.triu(np.ones((3, 3))))
+    Q, info = q.q_from_r(X0, R)
+    assert info_of(info) == [0, 0] and Q.shape == (0, 3)
+    W, C = q.project_out(torch.zeros((2, 0), dtype=torch.float64, device="cuda").T, X0)
+    assert W.shape == (0, 3) and np.all(to_host(C) == 0.0)
+    x = synth.gaussian(5000, 1, seed=8)
+    Qw, Rw, info = q.qr_wide(to_dev(x))
+    assert info_of(info) == [0, 0]
+    assert abs(to_host(Rw)[0, 0] - np.linalg.norm(x)) <= 1e-14 * np.linalg.norm(x)
+    assert np.max(np.abs(to_host(Qw)[:, 0] - x[:, 0] / np.linalg.norm(x))) <= 1e-14
+
+
 def test_svqb_z_factor():
     import paper_2603_20889_gb300 as q
 
