@@ -112,32 +112,26 @@ ql_status launch_one(const TsqrCall& c, const TreeView& tv_in, int gated) {
 }
 
 // Configuration table: NC (padded column count), TC column groups, RPT rows per thread,
-// T threads.  A thread holds RPT x NC/TC elements of the tile: 64 for n <= 8 (32 at n = 1),
-// 32 for n > 8, where 256-thread CTAs with twice the column groups measured 4-6 % faster
-// than 128-thread ones (m = 2^25: n = 64 146.4 vs 152.2 ms, n = 32 37.1 vs 38.7, n = 16
-// 9.76 vs 10.33).
+// T threads.  A thread holds RPT x NC/TC elements of the tile: 64 for n <= 8 (32 at n = 1)
+// and for n > 8, where 256-thread CTAs with 16 rows per thread measured fastest (m = 2^25:
+// n = 64 139.6 ms against 146.1 with 8 rows per thread and 216.2 with 512-thread CTAs;
+// n = 32 35.4 against 37.0; n = 16 9.46 against 9.75): a column reduction across the row
+// threads then serves twice the rows.
 template <typename S, typename Ar>
 ql_status dispatch(const TsqrCall& c, const TreeView& tv, int gated) {
   const int n = c.n;
   if constexpr (std::is_same<S, double>::value && std::is_same<Ar, ArithDF>::value) {
     const int v = tsqr_variant();  // alternative thread layouts (tuning experiments)
-    if (v > 0 && n > 4) {
-      if (n <= 8) {
-        if (v == 1) return launch_one<8, 1, 4, 256, S, Ar>(c, tv, gated);
-        if (v == 2) return launch_one<8, 2, 8, 256, S, Ar>(c, tv, gated);
-        if (v == 3) return launch_one<8, 2, 4, 128, S, Ar>(c, tv, gated);
-      } else if (n <= 16) {
-        if (v == 1) return launch_one<16, 2, 4, 256, S, Ar>(c, tv, gated);
+    if (v > 0 && n > 8) {
+      if (n <= 16) {
+        if (v == 1) return launch_one<16, 4, 8, 256, S, Ar>(c, tv, gated);
         if (v == 2) return launch_one<16, 2, 8, 128, S, Ar>(c, tv, gated);
-        if (v == 3) return launch_one<16, 1, 4, 128, S, Ar>(c, tv, gated);
       } else if (n <= 32) {
-        if (v == 1) return launch_one<32, 4, 4, 256, S, Ar>(c, tv, gated);
+        if (v == 1) return launch_one<32, 8, 8, 256, S, Ar>(c, tv, gated);
         if (v == 2) return launch_one<32, 4, 8, 128, S, Ar>(c, tv, gated);
-        if (v == 3) return launch_one<32, 2, 4, 128, S, Ar>(c, tv, gated);
       } else {
-        if (v == 1) return launch_one<64, 8, 4, 256, S, Ar>(c, tv, gated);
+        if (v == 1) return launch_one<64, 16, 8, 256, S, Ar>(c, tv, gated);
         if (v == 2) return launch_one<64, 8, 8, 128, S, Ar>(c, tv, gated);
-        if (v == 3) return launch_one<64, 4, 4, 128, S, Ar>(c, tv, gated);
       }
     }
   }
@@ -145,9 +139,9 @@ ql_status dispatch(const TsqrCall& c, const TreeView& tv, int gated) {
   if (n <= 2) return launch_one<2, 1, 32, 128, S, Ar>(c, tv, gated);
   if (n <= 4) return launch_one<4, 1, 16, 128, S, Ar>(c, tv, gated);
   if (n <= 8) return launch_one<8, 1, 8, 128, S, Ar>(c, tv, gated);
-  if (n <= 16) return launch_one<16, 4, 8, 256, S, Ar>(c, tv, gated);
-  if (n <= 32) return launch_one<32, 8, 8, 256, S, Ar>(c, tv, gated);
-  return launch_one<64, 16, 8, 256, S, Ar>(c, tv, gated);
+  if (n <= 16) return launch_one<16, 4, 16, 256, S, Ar>(c, tv, gated);
+  if (n <= 32) return launch_one<32, 8, 16, 256, S, Ar>(c, tv, gated);
+  return launch_one<64, 16, 16, 256, S, Ar>(c, tv, gated);
 }
 
 
