@@ -54,6 +54,29 @@ MEASURED_TRAFFIC_PER_ROW = {
 DF_INSTR_PER_PAIR = 27
 
 
+def rel_err(R, R_ref) -> float:
+    """||R - R_ref||_F / ||R_ref||_F, the accuracy measure of the batched and serving checks."""
+    import numpy as np
+
+    R, R_ref = np.asarray(R, dtype=np.float64), np.asarray(R_ref, dtype=np.float64)
+    den = float(np.linalg.norm(R_ref))
+    return float(np.linalg.norm(R - R_ref)) / (den if den > 0 else 1.0)
+
+
+def tolerance(n: int, kappa: float) -> float:
+    """The stated bound on rel_err for FP64 TSQR: 1e-13 n kappa(X)."""
+    return 1e-13 * n * max(float(kappa), 1.0)
+
+
+def lapack_r(X):
+    """R of X (m x n, host) from LAPACK's Householder QR, rows scaled to a nonnegative diagonal."""
+    import numpy as np
+
+    R = np.linalg.qr(np.asarray(X, dtype=np.float64), mode="r")
+    sg = np.where(np.diag(R) < 0.0, -1.0, 1.0)
+    return R * sg[:, None]
+
+
 def kernel_name(meth: str, n: int) -> str:
     if meth == "tsqr":
         return "tsqr_kernel"
@@ -360,6 +383,12 @@ def run_ours(args, rank, world, local_rank):
         except Exception as exc:
             extra["serving"] = {"error": repr(exc)[:300]}
         torch.cuda.empty_cache()
+        # the same stream below the sustained rate: latencies without an ever-growing queue
+        try:
+            extra["serving_300"] = run_serving(q, lib, torch, dev, count=3000, rate=300.0)
+        except Exception as exc:
+            extra["serving_300"] = {"error": repr(exc)[:300]}
+        torch.cuda.empty_cache()
     out = {
         "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True, "scaling": "weak",
@@ -608,7 +637,7 @@ def run_batched(q, lib, torch, dev, stream, count=512):
     """Uneven batch (m log-uniform in [2^10, 2^20], n in {4..48}, kappa log-uniform in
     [1, 1e6], FP64): one persistent launch (plain and CUDA-graph replay) against a loop of
     one TSQR launch per matrix on the same stream.  Accuracy: sampled instances against the
-    single-call results (same kernels) and the smallest against the CPU oracle."""
+    single-call results (same kernels) and the smallest against LAPACK's QR on the host."""
     import numpy as np
 
     from paper_2603_20889_gb300 import synth
@@ -659,22 +688,20 @@ def run_batched(q, lib, torch, dev, stream, count=512):
                               wsl.data_ptr(), wsl.numel(), sptr)
 
     ms_loop = timed(loop, 2)
-    # batched vs single-call parity on a sample, and the smallest instances vs the oracle
-    import oracle
-
+    # batched vs single-call parity on a sample, and the smallest instances against LAPACK's
+    # Householder QR on the host (the parity against the oracle is the tests' job)
     worst = 0.0
     for i in range(0, count, 16):
         it = insts[i]
         e = float((Rb[i] - outs[i][0]).norm() / outs[i][0].norm())
-        worst = max(worst, e / oracle.tolerance(it.n, max(it.kappa, 10.0)))
+        worst = max(worst, e / tolerance(it.n, max(it.kappa, 10.0)))
     small = sorted(range(count), key=lambda i: insts[i].m * insts[i].n)[:4]
-    worst_oracle = 0.0
+    worst_lapack = 0.0
     for i in small:
         it = insts[i]
         Xh = Xs[i].double().cpu().numpy().T
-        Rr = oracle.householder_r(Xh)
         Rh = Rb[i].cpu().numpy().T  # stored column-major
-        worst_oracle = max(worst_oracle, oracle.rel_err(Rh, Rr) / oracle.tolerance(it.n, max(it.kappa, 10.0)))
+        worst_lapack = max(worst_lapack, rel_err(Rh, lapack_r(Xh)) / tolerance(it.n, max(it.kappa, 10.0)))
     del Xs
     return {
         "workload": f"{count} uneven FP64 problems: m log-uniform in [2^10, 2^20], n in {{4..48}}, "
@@ -687,7 +714,7 @@ def run_batched(q, lib, torch, dev, stream, count=512):
         "ms_batched": round(ms_batch, 3), "ms_graph": round(ms_graph, 3), "ms_loop": round(ms_loop, 3),
         "eff_gbs_batched": round(total_bytes / (ms_graph / 1e3) / 1e9, 1),
         "status_errors": len(bad), "max_err_over_tol_vs_single": round(worst, 4),
-        "max_err_over_tol_vs_oracle": round(worst_oracle, 4),
+        "max_err_over_tol_vs_lapack": round(worst_lapack, 4),
     }
 
 
@@ -753,18 +780,16 @@ def run_serving(q, lib, torch, dev, count=20000, rate=2000.0, budget=60 << 30, m
             X = pool[:r.n, :r.m].T
         Ra, _ = q.tsqr_qless(X)
         Ra = Ra.cpu().numpy()
-        import oracle
-
-        worst = max(worst, oracle.rel_err(Rs, Ra) / oracle.tolerance(n1, max(r.kappa, 10.0)))
+        worst = max(worst, rel_err(Rs, Ra) / tolerance(n1, max(r.kappa, 10.0)))
     srv.close()
     del pools64, pools32
     return {
         "workload": f"Poisson {rate:.0f} req/s, m log-uniform in [2^12, 2^22], n in {{2..64}}, 30% FP32, "
-                    "20% least squares, kappa log-uniform in [1, 1e6], 60 GB budget",
+                    "20% least squares, kappa log-uniform in [1, 1e6], 60 GiB (64.4 GB) budget",
         "submitted": submitted, "completed": int(st.completed), "offered_s": round(t_sub, 2),
         "wall_s": round(t_all, 2), "solves_per_s": round(st.completed / max(t_all, 1e-9), 1),
         "p50_ms": round(st.p50_ms, 3), "p99_ms": round(st.p99_ms, 3), "mean_ms": round(st.mean_ms, 3),
-        "hbm_peak_gb": round(st.hbm_peak_bytes / 1e9, 2), "sample_status_errors": bad, "sample_failures": codes,
+        "hbm_budget_gb": round(budget / 1e9, 2), "hbm_peak_gb": round(st.hbm_peak_bytes / 1e9, 2), "sample_status_errors": bad, "sample_failures": codes,
         "max_err_over_tol_alone_vs_mix": round(worst, 4),
     }
 

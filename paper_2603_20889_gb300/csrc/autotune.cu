@@ -1,9 +1,11 @@
 // Project autotuner: for an (m, n, dtype, kappa) class it times the candidate
 // configurations on the current GPU -- TSQR with 1 or 2 CTAs per SM (which sets the
-// number of R-tree leaves and the rows per CTA) and Cholesky-QR2 when the condition hint
-// allows it (kappa <= 1e6, where the Gram method stays within the accuracy bound) -- and
-// records the fastest in a process-wide table that ql_autotune_choose() and the QL_AUTO
-// paths consult.  The table persists as a small JSON text file.
+// number of R-tree leaves and the rows per CTA; a request above what the registers allow
+// is clamped, so for n > 8, one CTA per SM, both are the same launch) and Cholesky-QR2
+// when the condition hint allows it (kappa <= 1e6, where the Gram method stays within the
+// accuracy bound) -- and records the fastest in a process-wide table that
+// ql_autotune_choose() and the QL_AUTO paths consult.  The table persists as a small JSON
+// text file.
 #include <chrono>
 #include <cmath>
 #include <cstdio>

@@ -87,79 +87,117 @@ QL_DEV void full_times_full(const double* A, int lda, const double* B, int ldb, 
 // Cyclic two-sided Jacobi on a symmetric matrix A (full storage, overwritten): on return
 // A's diagonal holds the eigenvalues and U (n x n) the eigenvectors, A_in = U diag U^T.
 // Rounds follow the round-robin ("chess tournament") ordering, so the n/2 rotations of a
-// round touch disjoint row/column pairs and run concurrently.  A pair is skipped when
-// |a_pq| <= 1e-17 sqrt(|a_pp a_qq|); the loop stops after a sweep without rotations or
-// after max_sweeps.  Returns the number of sweeps used.
+// round touch disjoint row/column pairs and run concurrently.  A round applies J^T A J by
+// 2 x 2 blocks: block (k1, k2), k1 <= k2, holds rows {p1, q1} and columns {p2, q2} of the
+// pairs k1 and k2, is rotated on both sides at once and is written together with its
+// mirror image, so only half of the blocks are computed (about 2/3 of the FP64 work of
+// rotating all columns, then all rows) and a round needs two barriers.  A rotated pair's
+// diagonal block takes the closed form a_pp - t a_pq, a_qq + t a_pq, 0.  For odd n the
+// matrix is bordered by a zero row and column (the dummy player of the ordering), which no
+// rotation touches, so A and U need n + 1 rows and columns of storage then.  A pair is
+// skipped when |a_pq| <= 1e-17 sqrt(|a_pp a_qq|); the loop stops after a sweep without
+// rotations or after max_sweeps.  Returns the number of sweeps used.
 template <int T>
 QL_DEV int jacobi_eig(double* A, int ld, double* U, int ldu, int n, double* sc, int* s_flag, int max_sweeps = 30) {
-  for (int t = threadIdx.x; t < n * n; t += T) U[(t / n) * ldu + t % n] = (t / n == t % n) ? 1.0 : 0.0;
+  if (n < 2) {
+    if (threadIdx.x == 0 && n == 1) U[0] = 1.0;
+    __syncthreads();
+    return 0;
+  }
   const int N = (n + 1) & ~1;  // players (one dummy when n is odd)
   const int half = N / 2;
+  const int nb = half * (half + 1) / 2;  // blocks k1 <= k2
+  for (int e = threadIdx.x; e < N * N; e += T) {
+    const int i = e / N, j = e % N;
+    U[i * ldu + j] = (i == j) ? 1.0 : 0.0;
+    if (i == n || j == n) A[i * ld + j] = 0.0;  // the border of odd n
+  }
   int sweep = 0;
   __syncthreads();
   for (; sweep < max_sweeps; ++sweep) {
     if (threadIdx.x == 0) *s_flag = 0;
     __syncthreads();
     for (int r = 0; r < N - 1; ++r) {
-      // rotation parameters, one thread per pair
+      // rotation parameters, one thread per pair: c, s, t and the pair (p << 8 | q)
       for (int k = threadIdx.x; k < half; k += T) {
-        int a = (k == 0) ? 0 : 1 + (k - 1 + r) % (N - 1);
-        int b = 1 + (N - 2 - k + r) % (N - 1);
-        int p = a < b ? a : b, q = a < b ? b : a;
-        double c = 1.0, s = 0.0;
-        if (q < n) {
-          double apq = A[p * ld + q], app = A[p * ld + p], aqq = A[q * ld + q];
-          if (apq != 0.0 && fabs(apq) > 1e-17 * sqrt(fabs(app * aqq))) {
-            double tau = (aqq - app) / (2.0 * apq);
-            double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-            c = 1.0 / sqrt(1.0 + t * t);
-            s = t * c;
-            *s_flag = 1;
-          }
+        const int a = (k == 0) ? 0 : 1 + (k - 1 + r) % (N - 1);
+        const int b = 1 + (N - 2 - k + r) % (N - 1);
+        const int p = a < b ? a : b, q = a < b ? b : a;
+        double c = 1.0, s = 0.0, t = 0.0;
+        const double apq = A[p * ld + q], app = A[p * ld + p], aqq = A[q * ld + q];
+        if (apq != 0.0 && fabs(apq) > 1e-17 * sqrt(fabs(app * aqq))) {
+          const double tau = (aqq - app) / (2.0 * apq);
+          t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+          c = 1.0 / sqrt(1.0 + t * t);
+          s = t * c;
+          *s_flag = 1;
         }
         sc[4 * k + 0] = c;
         sc[4 * k + 1] = s;
-        sc[4 * k + 2] = (double)p;
-        sc[4 * k + 3] = (double)q;
+        sc[4 * k + 2] = t;
+        sc[4 * k + 3] = (double)((p << 8) | q);
       }
       __syncthreads();
-      // columns p, q of A and U:  X <- X J
-      for (int t = threadIdx.x; t < half * n; t += T) {
-        int k = t / n, i = t % n;
-        double c = sc[4 * k], s = sc[4 * k + 1];
-        int p = (int)sc[4 * k + 2], q = (int)sc[4 * k + 3];
-        if (q < n && s != 0.0) {
-          double x = A[i * ld + p], y = A[i * ld + q];
-          A[i * ld + p] = c * x - s * y;
-          A[i * ld + q] = s * x + c * y;
-          double u = U[i * ldu + p], v = U[i * ldu + q];
-          U[i * ldu + p] = c * u - s * v;
-          U[i * ldu + q] = s * u + c * v;
-        }
-      }
-      __syncthreads();
-      // rows p, q of A:  A <- J^T A
-      for (int t = threadIdx.x; t < half * n; t += T) {
-        int k = t / n, i = t % n;
-        double c = sc[4 * k], s = sc[4 * k + 1];
-        int p = (int)sc[4 * k + 2], q = (int)sc[4 * k + 3];
-        if (q < n && s != 0.0) {
-          double x = A[p * ld + i], y = A[q * ld + i];
-          A[p * ld + i] = c * x - s * y;
-          A[q * ld + i] = s * x + c * y;
-        }
-      }
-      __syncthreads();
-      for (int k = threadIdx.x; k < half; k += T) {
-        int p = (int)sc[4 * k + 2], q = (int)sc[4 * k + 3];
-        if (q < n && sc[4 * k + 1] != 0.0) {
-          A[p * ld + q] = 0.0;
-          A[q * ld + p] = 0.0;
+      // A <- J^T A J by blocks (first nb work items), U <- U J by (pair, row) (the rest)
+      for (int w = threadIdx.x; w < nb + half * N; w += T) {
+        if (w < nb) {
+          int k2 = (int)((sqrtf(8.0f * (float)w + 1.0f) - 1.0f) * 0.5f);
+          while (k2 * (k2 + 1) / 2 > w) --k2;
+          while ((k2 + 1) * (k2 + 2) / 2 <= w) ++k2;
+          const int k1 = w - k2 * (k2 + 1) / 2;
+          const double s1 = sc[4 * k1 + 1], s2 = sc[4 * k2 + 1];
+          const int pq1 = (int)sc[4 * k1 + 3], pq2 = (int)sc[4 * k2 + 3];
+          const int p1 = pq1 >> 8, q1 = pq1 & 255, p2 = pq2 >> 8, q2 = pq2 & 255;
+          if (k1 == k2) {
+            if (s1 != 0.0) {
+              const double t1 = sc[4 * k1 + 2], apq = A[p1 * ld + q1];
+              A[p1 * ld + p1] = fma(-t1, apq, A[p1 * ld + p1]);
+              A[q1 * ld + q1] = fma(t1, apq, A[q1 * ld + q1]);
+              A[p1 * ld + q1] = 0.0;
+              A[q1 * ld + p1] = 0.0;
+            }
+          } else if (s1 != 0.0 || s2 != 0.0) {
+            double b00 = A[p1 * ld + p2], b01 = A[p1 * ld + q2], b10 = A[q1 * ld + p2], b11 = A[q1 * ld + q2];
+            if (s2 != 0.0) {  // columns p2, q2
+              const double c2 = sc[4 * k2];
+              const double x0 = b00, x1 = b10;
+              b00 = c2 * x0 - s2 * b01;
+              b01 = s2 * x0 + c2 * b01;
+              b10 = c2 * x1 - s2 * b11;
+              b11 = s2 * x1 + c2 * b11;
+            }
+            if (s1 != 0.0) {  // rows p1, q1
+              const double c1 = sc[4 * k1];
+              const double y0 = b00, y1 = b01;
+              b00 = c1 * y0 - s1 * b10;
+              b10 = s1 * y0 + c1 * b10;
+              b01 = c1 * y1 - s1 * b11;
+              b11 = s1 * y1 + c1 * b11;
+            }
+            A[p1 * ld + p2] = b00;
+            A[p2 * ld + p1] = b00;
+            A[p1 * ld + q2] = b01;
+            A[q2 * ld + p1] = b01;
+            A[q1 * ld + p2] = b10;
+            A[p2 * ld + q1] = b10;
+            A[q1 * ld + q2] = b11;
+            A[q2 * ld + q1] = b11;
+          }
+        } else {
+          const int v = w - nb, k = v / N, i = v % N;
+          const double s = sc[4 * k + 1];
+          if (s != 0.0) {
+            const double c = sc[4 * k];
+            const int pq = (int)sc[4 * k + 3], p = pq >> 8, q = pq & 255;
+            const double u = U[i * ldu + p], x = U[i * ldu + q];
+            U[i * ldu + p] = c * u - s * x;
+            U[i * ldu + q] = s * u + c * x;
+          }
         }
       }
       __syncthreads();
     }
-    int any = *s_flag;
+    const int any = *s_flag;
     __syncthreads();
     if (!any) break;
   }
