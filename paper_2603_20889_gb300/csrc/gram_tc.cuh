@@ -10,9 +10,10 @@
 // Every digit is an integer that bf16 holds exactly, every product d_p d_q < 2^14 is exact,
 // and the tensor cores sum at most 7 digit pairs over at most 128 rows per accumulator,
 // which stays below 2^24: every FP32 accumulator is an exact integer.  Products with the
-// same weight d = p + q (p + q <= 8, the terms above 2^-56 of the leading one) share one
-// accumulator; each is scaled by 2^(e_i + e_j - 7d) (exact) and added into a double-float
-// accumulator per C entry.
+// same weight d = p + q share one accumulator, for p + q <= 8 (the weights down to 2^-56;
+// the dropped pairs, p + q >= 9, add up to less than 2^-46 of 2^(e_i + e_j) per row); each
+// is scaled by 2^(e_i + e_j - 7d) (exact) and added into a double-float accumulator per C
+// entry.
 //
 // The second pass forms Y = X M (M = R1^{-1} or B1) on the tensor cores as well.  X is sliced
 // at the column scale e_k of the whole matrix (the first pass records it), so that
