@@ -357,6 +357,11 @@ def run_ours(args, rank, world, local_rank):
             extra["scholqr3"] = {"error": repr(exc)[:300]}
         torch.cuda.empty_cache()
         try:
+            extra["kappa_rows"] = run_kappa_rows(q, lib, torch, dev, stream)
+        except Exception as exc:
+            extra["kappa_rows"] = {"error": repr(exc)[:300]}
+        torch.cuda.empty_cache()
+        try:
             extra["q_from_r"] = run_qform(q, lib, torch, dev, stream)
         except Exception as exc:
             extra["q_from_r"] = {"error": repr(exc)[:300]}
@@ -541,6 +546,46 @@ def run_scholqr3(q, lib, torch, dev, stream, reps=3):
                              "rel_diff_vs_tsqr": diff, "tolerance_1e-13_n_kappa": 1e-13 * n * 1e8})
         del X, Xt, ws
         torch.cuda.empty_cache()
+    return out
+
+
+def run_kappa_rows(q, lib, torch, dev, stream, reps=2):
+    """The condition sweep's other kappa values (1 and 1e8) at n = 16 and 64: time per call
+    of TSQR, Cholesky-QR2 and SVQB2, their status, and the relative difference of each
+    Gram method's R from TSQR's (held to 1e-13 n kappa only for kappa <= 1e6; at 1e8 the
+    Gram methods square a condition number beyond 1 / sqrt(u) and may report breakdown)."""
+    from paper_2603_20889_gb300 import synth
+
+    out = {"workload": "X = G S, m = 2^25, kappa in {1, 1e8}, FP64 storage", "calls": []}
+    for kappa in (1.0, 1e8):
+        for n in (16, 64):
+            X = synth.conditioned_device(M, n, kappa, seed=6000 + 2 * n + (1 if kappa > 1.0 else 0), device=dev)
+            Xt = X.T
+            ws = q.workspace(q.QL_AUTO, M, n, q.QL_F64, dev)
+            Rt, it = q.tsqr_qless(Xt, ws=ws)
+            Rc, ic = q.cholqr2_qless(Xt, ws=ws)
+            Rs, _, iv = q.svqb_qless(Xt, ws=ws)
+            calls = (("tsqr", lambda: q.tsqr_qless(Xt, Rt, it, ws)),
+                     ("cholqr2", lambda: q.cholqr2_qless(Xt, Rc, ic, ws)),
+                     ("svqb2", lambda: q.svqb_qless(Xt, Rs, info=iv, ws=ws)))
+            row = {"kappa": kappa, "n": n}
+            for name, fn in calls:
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(reps):
+                    fn()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                row[name + "_ms"] = round(e0.elapsed_time(e1) / reps, 3)
+            row["status"] = {"tsqr": it.tolist(), "cholqr2": ic.tolist(), "svqb2": iv.tolist()}
+            for name, R in (("cholqr2", Rc), ("svqb2", Rs)):
+                d = float(torch.linalg.norm(R - Rt) / torch.linalg.norm(Rt))
+                row[name + "_rel_diff_vs_tsqr"] = d if math.isfinite(d) else None
+            row["tolerance_1e-13_n_kappa"] = 1e-13 * n * kappa
+            out["calls"].append(row)
+            del X, Xt, ws, Rt, Rc, Rs
+            torch.cuda.empty_cache()
     return out
 
 
