@@ -116,7 +116,8 @@ ql_status launch_one(const TsqrCall& c, const TreeView& tv_in, int gated) {
 // and for n > 8, where 256-thread CTAs with 16 rows per thread measured fastest (m = 2^25:
 // n = 64 139.6 ms against 146.1 with 8 rows per thread and 216.2 with 512-thread CTAs;
 // n = 32 35.4 against 37.0; n = 16 9.46 against 9.75): a column reduction across the row
-// threads then serves twice the rows.
+// threads then serves twice the rows.  512-thread CTAs with the same 16 rows per thread and
+// half the columns measured slower again (n = 64 154.4 ms, n = 32 60.1 or 40.1, n = 16 15.5).
 template <typename S, typename Ar>
 ql_status dispatch(const TsqrCall& c, const TreeView& tv, int gated) {
   const int n = c.n;
