@@ -93,7 +93,10 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--e2e-steps", type=int, default=5)
+    # the first end-to-end step fills the copy pipeline (nothing to overlap its copies with,
+    # and host -> device copies run at a fraction of the link rate while the GPU idles):
+    # ten steps spread that fill the way a long run does
+    p.add_argument("--e2e-steps", type=int, default=10)
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--no-batched", dest="batched", action="store_false")
     p.add_argument("--no-serving", dest="serving", action="store_false")
@@ -446,9 +449,12 @@ def run_e2e(args, q, lib, torch, dev, Xs, ws, wsb, stream, ls):
     ls_used = {k: _t.cuda.Event() for k in hls}
 
     def copy_in(dst, src):
-        """Host -> device in 1 GB pieces alternating over the two copy streams."""
+        """Host -> device in pieces of at most 1 GB alternating over the two copy streams; at
+        least two pieces, so that both streams carry every matrix (a matrix's factorisations
+        wait for its last piece)."""
         d, h = dst.view(-1), src.reshape(-1)
-        ch = (1 << 30) // h.element_size()
+        pieces = max(2, -(-h.numel() * h.element_size() // (1 << 30)))
+        ch = -(-h.numel() // pieces)
         for k, i in enumerate(range(0, h.numel(), ch)):
             with _t.cuda.stream(cstreams[k % 2]):
                 d[i:i + ch].copy_(h[i:i + ch], non_blocking=True)
@@ -509,10 +515,11 @@ def run_e2e(args, q, lib, torch, dev, Xs, ws, wsb, stream, ls):
     bytes_step = sum(8.0 * M * n * len(METHODS) for n in NS) + 12.0 * LS_M * (LS_N + 1)
     del host, bufd, hls
     return {"value": round(bytes_step / (ms / 1e3) / 1e9, 2), "unit": "GB/s", "h2d_bytes_per_step": int(h2d),
-            "d2h_bytes_per_step": int(d2h), "ms_per_step": round(ms, 3),
-            "note": "each X (and each [A b]) copied host->device once per step from pinned memory in 1 GB "
-                    "pieces alternating over two copy streams into its own device buffer, so copies overlap "
-                    "the factorisations still running (also the previous step's); every R and x read back"}
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": round(ms, 3), "steps": args.e2e_steps,
+            "note": "each X (and each [A b]) copied host->device once per step from pinned memory in pieces of "
+                    "at most 1 GB (two at least) alternating over two copy streams into its own device buffer, so "
+                    "copies overlap the factorisations still running (also the previous step's); every R and x "
+                    "read back"}
 
 
 # ------------------------------------------------------------------ shifted Cholesky-QR3
