@@ -1,6 +1,6 @@
 """GPU parity: the CUDA path (through the C ABI) against the CPU oracle, element by element.
 
-Bar (BASELINE the benchmark spec): ||R - R_ref||_F / ||R_ref||_F <= 1e-13 * n * kappa(X) for TSQR;
+Bar: ||R - R_ref||_F / ||R_ref||_F <= 1e-13 * n * kappa(X) for FP64 TSQR;
 Cholesky-QR2 and SVQB2 are held to the same bound for kappa <= 1e6.  Sizes span several
 row tiles per CTA and ragged tails; both the double-float default and the native FP64
 arithmetic are checked.
