@@ -348,7 +348,7 @@ def run_ours(args, rank, world, local_rank):
                         note="per-launch time from CUDA events around the call on its stream; Gram methods: "
                              "call time / 2 passes")
 
-    e2e = run_e2e(args, q, lib, torch, dev, Xs, ws, wsb, stream, ls) if args.e2e_steps > 0 else None
+    e2e = run_e2e(args, q, lib, torch, dev, Xs, ws, wsb, stream, ls, world) if args.e2e_steps > 0 else None
     del ls, At, bvec
     del Xs
     torch.cuda.empty_cache()
@@ -414,7 +414,7 @@ def run_ours(args, rank, world, local_rank):
     return out
 
 
-def run_e2e(args, q, lib, torch, dev, Xs, ws, wsb, stream, ls):
+def run_e2e(args, q, lib, torch, dev, Xs, ws, wsb, stream, ls, world=1):
     """The same sweep through the C ABI from HOST buffers: every step copies each X from
     pinned host memory to the device (two copy streams, one device buffer per matrix, so
     copies overlap the factorisations still running) and reads every R back, all inside
@@ -512,10 +512,13 @@ def run_e2e(args, q, lib, torch, dev, Xs, ws, wsb, stream, ls):
     e1.record(stream)
     _t.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.e2e_steps
-    bytes_step = sum(8.0 * M * n * len(METHODS) for n in NS) + 12.0 * LS_M * (LS_N + 1)
+    if world > 1:  # replicas: the slowest rank's time, every rank's bytes
+        _t.distributed.barrier()
+        ms = max_over_ranks(ms, dev)
+    bytes_step = world * (sum(8.0 * M * n * len(METHODS) for n in NS) + 12.0 * LS_M * (LS_N + 1))
     del host, bufd, hls
-    return {"value": round(bytes_step / (ms / 1e3) / 1e9, 2), "unit": "GB/s", "h2d_bytes_per_step": int(h2d),
-            "d2h_bytes_per_step": int(d2h), "ms_per_step": round(ms, 3), "steps": args.e2e_steps,
+    return {"value": round(bytes_step / (ms / 1e3) / 1e9, 2), "unit": "GB/s", "h2d_bytes_per_step": int(world * h2d),
+            "d2h_bytes_per_step": int(world * d2h), "ms_per_step": round(ms, 3), "steps": args.e2e_steps,
             "note": "each X (and each [A b]) copied host->device once per step from pinned memory in pieces of "
                     "at most 1 GB (two at least) alternating over two copy streams into its own device buffer, so "
                     "copies overlap the factorisations still running (also the previous step's); every R and x "
