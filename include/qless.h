@@ -100,13 +100,15 @@ ql_status ql_tsqr_qless(int64_t m, int64_t n, const void* X, ql_dtype dtype, int
 
 /*
  * TSQR for callers that cannot allocate device memory (the paper has no counterpart: it is
- * an interface addition of this library).  Same computation and arguments as
+ * an interface addition of this library).  Same computation, arguments, argument and
+ * alignment checks (QL_ERR_ARG, QL_ERR_ALIGN before any device work) and tuned grid as
  * ql_tsqr_qless, without the workspace: code running while its stream is captured into a
  * CUDA graph may not call cudaMalloc, host callbacks must not, and extensions of
  * frameworks that route every device allocation through their own pools often have no
  * allocator to call.  The scratch lives in a fixed 4 MiB array inside the library that
  * every GPU loading the library keeps until the process exits; n <= 16 is supported (any
- * m), larger n returns QL_ERR_WORKSPACE.  No cudaMalloc, cudaFree or other allocating
+ * m), larger n returns QL_ERR_WORKSPACE (the capacity check uses the SM count of the device
+ * current at the call).  No cudaMalloc, cudaFree or other allocating
  * call is made.  The first call on a device looks up the array's device address (with that
  * device current) and should come before any stream capture.  All calls share the one
  * array: calls that overlap on the GPU (different streams, or different host threads)

@@ -8,25 +8,28 @@
 
 namespace ql {
 
-constexpr int kApiMaxN = 64;  // largest n any entry point accepts
-
 static std::atomic<int> g_arith{QL_ARITH_DF};
 static std::atomic<unsigned long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 ql_arith current_arith() { return (ql_arith)g_arith.load(); }
 
-static bool elem_aligned(const void* p, ql_dtype dt) {
+bool elem_aligned(const void* p, ql_dtype dt) {
   uintptr_t a = (uintptr_t)p;
   return dt == QL_F64 ? (a % 8 == 0) : (a % 4 == 0);
 }
 
-static ql_status check_matrix(int64_t m, int64_t n, const void* X, ql_dtype dt, int64_t ld, int nmax) {
+ql_status check_matrix(int64_t m, int64_t n, const void* X, ql_dtype dt, int64_t ld, int nmax) {
   if (m < 0 || n < 1 || n > nmax) return QL_ERR_ARG;
   if (dt != QL_F64 && dt != QL_F32) return QL_ERR_ARG;
   if (ld < (m > 1 ? m : 1)) return QL_ERR_ARG;
   if (m > 0 && !X) return QL_ERR_ARG;
   if (X && !elem_aligned(X, dt)) return QL_ERR_ALIGN;
   return QL_OK;
+}
+
+ql_status check_r(const double* R, int64_t ldr, int64_t n) {
+  if (!R || ldr < n) return QL_ERR_ARG;
+  return ((uintptr_t)R % 8) ? QL_ERR_ALIGN : QL_OK;
 }
 
 }  // namespace ql
@@ -63,7 +66,7 @@ ql_status ql_tsqr_qless(int64_t m, int64_t n, const void* X, ql_dtype dtype, int
                         int64_t ldr, int32_t* info, void* ws, size_t ws_bytes, void* stream) {
   ql_status st = check_matrix(m, n, X, dtype, ldx, kApiMaxN);
   if (st) return st;
-  if (!R || ldr < n || ((uintptr_t)R % 8)) return R ? QL_ERR_ALIGN : QL_ERR_ARG;
+  if ((st = check_r(R, ldr, n))) return st;
   TsqrCall c;
   c.m = m;
   c.n = (int)n;
@@ -89,7 +92,7 @@ static ql_status gram_entry(int method, int64_t m, int64_t n, const void* X, ql_
                             size_t ws_bytes, void* stream) {
   ql_status st = check_matrix(m, n, X, dtype, ldx, kApiMaxN);
   if (st) return st;
-  if (!R || ldr < n) return QL_ERR_ARG;
+  if ((st = check_r(R, ldr, n))) return st;
   GramCall c;
   c.m = m;
   c.n = (int)n;

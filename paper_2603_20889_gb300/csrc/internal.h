@@ -66,8 +66,19 @@ struct GramCall {
 size_t gram_workspace_bytes(int n);
 ql_status gram_launch(const GramCall& c, ql_arith arith);
 
+// SM count of the current device (cached per device).
 int device_sm_count();
 ql_arith current_arith();
+
+// Largest n any entry point accepts.
+constexpr int kApiMaxN = 64;
+// Argument checks shared by the entry points (no device work): m >= 0, 1 <= n <= nmax, a
+// known dtype, ld >= max(m, 1), X non-null when m > 0 (QL_ERR_ARG), X aligned to its
+// element size (QL_ERR_ALIGN).
+bool elem_aligned(const void* p, ql_dtype dt);
+ql_status check_matrix(int64_t m, int64_t n, const void* X, ql_dtype dt, int64_t ld, int nmax);
+// Output triangle R: non-null with ldr >= n (QL_ERR_ARG), 8-byte aligned (QL_ERR_ALIGN).
+ql_status check_r(const double* R, int64_t ldr, int64_t n);
 // Whether the Gram passes use the tensor-core kernels (double-float mode, n >= 9);
 // the environment variable QL_GRAM_SIMT=1 selects the SIMT kernels instead.
 bool tc_gram_enabled();

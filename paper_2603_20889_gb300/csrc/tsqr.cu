@@ -5,6 +5,7 @@
 // completes the root writes R (or solves the least-squares problem of [A b]).  When the
 // double-float launch finds data outside its exponent range it leaves R unwritten and
 // raises a flag; the FP64 launch queued behind it runs only in that case.
+#include <atomic>
 #include <cstdlib>
 
 #include "tsqr_launch.cuh"
@@ -20,15 +21,16 @@ int tsqr_variant() {
 }
 
 int device_sm_count() {
-  static int sms = 0;
-  static std::once_flag once;
-  std::call_once(once, [] {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 1;
-  });
-  return sms;
+  // cached per device: a process may drive GPUs with different SM counts
+  constexpr int kMaxDev = 64;
+  static std::atomic<int> sms[kMaxDev] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) dev = 0;
+  int v = sms[dev].load(std::memory_order_relaxed);
+  if (v > 0) return v;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 1;
+  sms[dev].store(v, std::memory_order_relaxed);
+  return v;
 }
 
 size_t tsqr_workspace_bytes(int n) {

@@ -46,13 +46,15 @@ using namespace ql;
 
 extern "C" ql_status ql_tsqr_qless_noalloc(int64_t m, int64_t n, const void* X, ql_dtype dtype, int64_t ldx,
                                            double* R, int64_t ldr, int32_t* info, void* stream) {
-  if (m < 0 || n < 1 || (dtype != QL_F64 && dtype != QL_F32) || ldx < (m > 1 ? m : 1) || (m > 0 && !X) || !R ||
-      ldr < n)
-    return QL_ERR_ARG;
+  // the same argument and alignment checks as ql_tsqr_qless, before any device work
+  ql_status st = check_matrix(m, n, X, dtype, ldx, kApiMaxN);
+  if (st) return st;
+  if ((st = check_r(R, ldr, n))) return st;
   if (n > kNoAllocMaxN) return QL_ERR_WORKSPACE;  // beyond what the fixed scratch array holds
+  // the R-tree is sized for the SM count of the current device
   if (tsqr_workspace_bytes((int)n) > kNoAllocScratchBytes) return QL_ERR_WORKSPACE;
   void* scratch = nullptr;
-  ql_status st = scratch_for_current_device(&scratch);
+  st = scratch_for_current_device(&scratch);
   if (st != QL_OK) return st;
   TsqrCall c;
   c.m = m;
@@ -69,6 +71,8 @@ extern "C" ql_status ql_tsqr_qless_noalloc(int64_t m, int64_t n, const void* X, 
   c.ws = scratch;
   c.ws_bytes = kNoAllocScratchBytes;
   c.stream = (cudaStream_t)stream;
+  int ctas = 0;  // the autotuned grid, as the regular entry point uses (a table lookup, no allocation)
+  if (tune_lookup(m, n, dtype, 1.0, nullptr, &ctas)) c.ctas_per_sm = ctas;
   // tsqr_launch clears the counters and flags of the scratch on the stream before the
   // kernels run; the triangle slots are fully written before they are read.
   return tsqr_launch(c, current_arith());

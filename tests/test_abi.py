@@ -63,6 +63,16 @@ def test_host_only_calls(lib):
                            None) == q.QL_ERR_ALIGN
     assert L.ql_lstsq_qless(10, 64, ctypes.c_void_p(16), 10, ctypes.c_void_p(16), q.QL_F64, q.QL_TSQR,
                             ctypes.c_void_p(16), ctypes.c_void_p(16), None, None, None, 0, None) == q.QL_ERR_ARG
+    # the workspace-free TSQR makes the same checks before any device work
+    V = ctypes.c_void_p
+    assert L.ql_tsqr_qless_noalloc(10, 3, V(12), q.QL_F64, 10, V(16), 3, None, None) == q.QL_ERR_ALIGN
+    assert L.ql_tsqr_qless_noalloc(10, 3, V(16), q.QL_F64, 10, V(20), 3, None, None) == q.QL_ERR_ALIGN
+    assert L.ql_tsqr_qless_noalloc(10, 3, V(18), q.QL_F32, 10, V(16), 3, None, None) == q.QL_ERR_ALIGN
+    assert L.ql_tsqr_qless_noalloc(10, 3, V(16), q.QL_F64, 5, V(16), 3, None, None) == q.QL_ERR_ARG
+    assert L.ql_tsqr_qless_noalloc(10, 3, V(16), q.QL_F64, 10, None, 3, None, None) == q.QL_ERR_ARG
+    assert L.ql_tsqr_qless_noalloc(10, 65, V(16), q.QL_F64, 10, V(16), 65, None, None) == q.QL_ERR_ARG
+    # the Gram methods check R's alignment as well
+    assert L.ql_cholqr2_qless(10, 3, V(16), q.QL_F64, 10, V(20), 3, None, None, 0, None) == q.QL_ERR_ALIGN
     assert L.ql_server_create(0, 1, 1) is None
     assert L.ql_autotune_choose(1 << 20, 8, q.QL_F64, 1e9) == q.QL_TSQR
 

@@ -1,7 +1,8 @@
 """The workspace-free TSQR entry point, for callers that cannot allocate device memory
 (inside CUDA-graph capture, in host callbacks, or in framework plugins whose host owns
-every allocation).  It must give the same R as the regular entry point, call after call,
-although every call reuses the same library-owned scratch array.
+every allocation).  It must give the same R as the regular entry point, and the oracle's R
+within the parity tolerance, call after call, although every call reuses the same
+library-owned scratch array.
 
 Collected last on purpose (file name), so a stop-at-first-failure run has already run
 every other test; it also passes alone in a fresh process.
@@ -52,11 +53,13 @@ def test_noalloc_matches_regular_entry_twice(q, m, n, kappa, dtype):
     R_ref, info_ref = q.tsqr_qless(Xd)
     R_ref = to_host(R_ref)
     assert info_of(info_ref) == [0, 0]
+    R_or = oracle.householder_r(X.astype(np.float64))  # the stored (possibly float-rounded) X
     tol = oracle.tolerance(n, kappa)
     for _ in range(2):  # the shared scratch keeps the previous call's contents
         R, info = _noalloc(q, Xd, n)
         assert info == [0, 0]
         assert oracle.rel_err(R, R_ref) <= tol
+        assert oracle.rel_err(R, R_or) <= tol
 
 
 def test_noalloc_rejects_columns_beyond_its_scratch(q):
