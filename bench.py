@@ -63,6 +63,19 @@ def rel_err(R, R_ref) -> float:
     return float(np.linalg.norm(R - R_ref)) / (den if den > 0 else 1.0)
 
 
+def row_err(R, R_ref) -> float:
+    """max_ij |R_ij - R_ref_ij| / |R_ref_ii| over the upper triangle (rows with a zero
+    reference diagonal scaled by ||R_ref||_F): every entry against its row's diagonal."""
+    import numpy as np
+
+    R, R_ref = np.asarray(R, dtype=np.float64), np.asarray(R_ref, dtype=np.float64)
+    fro = float(np.linalg.norm(R_ref)) or 1.0
+    d = np.abs(np.diag(R_ref)).copy()
+    d[d == 0] = fro
+    D = np.triu(np.abs(R - R_ref)) / d[:, None]
+    return float(D.max()) if D.size else 0.0
+
+
 def tolerance(n: int, kappa: float) -> float:
     """The stated bound on rel_err for FP64 TSQR: 1e-13 n kappa(X)."""
     return 1e-13 * n * max(float(kappa), 1.0)
@@ -100,6 +113,10 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--no-batched", dest="batched", action="store_false")
     p.add_argument("--no-serving", dest="serving", action="store_false")
+    p.add_argument("--no-cpu-context", dest="cpu_context", action="store_false",
+                   help="skip the all-core torch.linalg.qr context number")
+    p.add_argument("--no-accuracy", dest="accuracy", action="store_false",
+                   help="skip the full-size accuracy check of the default arithmetic against native FP64")
     p.add_argument("--no-next", dest="next_rows", action="store_false",
                    help="skip the measurements of the rows beyond the sweep (shifted Cholesky-QR3, Q = X R^-1, "
                         "two-phase orthogonalisation, n > 64)")
@@ -326,19 +343,34 @@ def run_ours(args, rank, world, local_rank):
     hbm_view = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "peak_source": peak_kind}
     kname = f"{kernel_name(dmeth, dn)} ({dmeth}, n={dn}, m=2^25)"
+    # measured compute-pipe peaks of this GPU (FP32 / FP64 FMA, FP64 MMA, the library's
+    # double-float multiply-accumulate), the denominators of the arithmetic-bound rooflines
+    try:
+        peaks = {k: round(v, 3) for k, v in q.measure_peaks(stream).items()}
+        peaks["unit"] = "TFLOP/s"
+    except Exception as exc:
+        peaks = {"error": repr(exc)[:200]}
     if dmeth == "tsqr" and dn > 1:
         # the double-float Householder is bound by the FP32 pipes: 2 m n^2 FP64-equivalent
-        # flops per launch against what 128 FP32 lanes x SMs x clock deliver at 27 FP32
+        # flops per launch against the measured FP32 FMA instruction rate at 27 FP32
         # instructions per (dot, update) pair of 4 flops
         flops = 2.0 * M * dn * dn
         ach = flops / (kern_ms / 1e3) / 1e12
-        sms = torch.cuda.get_device_properties(dev).multi_processor_count
-        clk_hz = float(clk.get("sm_max_mhz") or 2070.0) * 1e6
-        alu_peak = sms * 128 * clk_hz / (DF_INSTR_PER_PAIR / 4.0) / 1e12
+        if "fp32_fma" in peaks:
+            alu_peak = peaks["fp32_fma"] / 2.0 * 4.0 / DF_INSTR_PER_PAIR
+            src = "measured"
+            deriv = (f"measured FP32 FMA rate {peaks['fp32_fma']} TFLOP/s = {peaks['fp32_fma'] / 2:.2f} T instr/s, "
+                     f"x 4 FP64-equivalent flops per {DF_INSTR_PER_PAIR} FP32 instructions (one dot + update pair)")
+        else:
+            sms = torch.cuda.get_device_properties(dev).multi_processor_count
+            clk_hz = float(clk.get("sm_max_mhz") or 2070.0) * 1e6
+            alu_peak = sms * 128 * clk_hz / (DF_INSTR_PER_PAIR / 4.0) / 1e12
+            src = "derived"
+            deriv = (f"{sms} SMs x 128 FP32 lanes x {clk_hz / 1e6:.0f} MHz / "
+                     f"({DF_INSTR_PER_PAIR} FP32 instructions per 4 FP64-equivalent flops)")
         roofline = {"bound": "alu", "achieved": round(ach, 3), "peak": round(alu_peak, 3), "unit": "TFLOP/s",
-                    "frac": round(ach / alu_peak, 4), "traffic": traffic, "peak_source": "derived",
-                    "peak_derivation": f"{sms} SMs x 128 FP32 lanes x {clk_hz / 1e6:.0f} MHz / "
-                                       f"({DF_INSTR_PER_PAIR} FP32 instructions per 4 FP64-equivalent flops)",
+                    "frac": round(ach / alu_peak, 4), "traffic": traffic, "peak_source": src,
+                    "peak_derivation": deriv,
                     "kernel": kname, "algorithmic_flops_per_launch": int(flops),
                     "algorithmic_bytes_per_launch": int(nbytes(dmeth, dn)), "hbm": hbm_view,
                     "note": "per-launch time from CUDA events around the call on its stream"}
@@ -349,6 +381,13 @@ def run_ours(args, rank, world, local_rank):
                              "call time / 2 passes")
 
     e2e = run_e2e(args, q, lib, torch, dev, Xs, ws, wsb, stream, ls, world) if args.e2e_steps > 0 else None
+    accuracy = None
+    if args.accuracy:
+        try:
+            accuracy = run_accuracy(q, lib, torch, dev, stream, Xs)
+        except Exception as exc:
+            accuracy = {"error": repr(exc)[:300]}
+        torch.cuda.empty_cache()
     del ls, At, bvec
     del Xs
     torch.cuda.empty_cache()
@@ -406,10 +445,12 @@ def run_ours(args, rank, world, local_rank):
                    "l2": "every input > L2 (>= 268 MB); no flush needed"},
         "roofline": roofline, "clocks": clk, "gpu_launches": int(launches),
         "gpu_launches_per_step": int(launches) // max(args.steps, 1),
-        "sweep": sweep, "status_errors": bad,
+        "sweep": sweep, "status_errors": bad, "compute_peaks": peaks,
     }
     if e2e:
         out["e2e"] = e2e
+    if accuracy:
+        out["accuracy"] = accuracy
     out.update(extra)
     return out
 
@@ -526,6 +567,71 @@ def run_e2e(args, q, lib, torch, dev, Xs, ws, wsb, stream, ls, world=1):
 
 
 # ------------------------------------------------------------------ shifted Cholesky-QR3
+
+
+def _factor(q, meth, Xt, ws, arith):
+    """R (host, float64) and status of one call in the given arithmetic."""
+    prev = q.set_arith(arith)
+    try:
+        if meth == "tsqr":
+            R, info = q.tsqr_qless(Xt, ws=ws)
+        elif meth == "cholqr2":
+            R, info = q.cholqr2_qless(Xt, ws=ws)
+        else:
+            R, _, info = q.svqb_qless(Xt, ws=ws)
+        Rh, st = R.cpu().numpy(), info.cpu().tolist()
+    finally:
+        q.set_arith(prev)
+    return Rh, st
+
+
+def run_accuracy(q, lib, torch, dev, stream, Xs):
+    """Is the default arithmetic FP64-class at full size?  Every sweep call (m = 2^25, n in
+    NS, TSQR / Cholesky-QR2 / SVQB2) is made in the default arithmetic (double-float
+    m-loops, FP64 n x n) and in native FP64 (every operation an FP64 instruction):
+      * on the sweep's own X = G S (kappa 1e4): the relative difference of the two;
+      * on X = H[:, J] R0, random Hadamard columns times a short-mantissa triangle with
+        kappa(R0) ~ 1e4, exact in FP64 and with R = sqrt(m) R0 exactly: each arithmetic's
+        error against that R, Frobenius and row-scaled, and their ratio.
+    The native-FP64 arm is the same kernels' FP64 instantiation (plain FP64 sums), so the
+    ratio answers "how far from what FP64 arithmetic gives in this design"."""
+    import numpy as np
+
+    from paper_2603_20889_gb300 import synth
+
+    t0 = time.time()
+    out = {"note": "default = double-float m-loops, FP64 n x n; f64 = native FP64 everywhere",
+           "gauss": [], "exact": [],
+           "exact_workload": "X = H[:, J] R0 (J random Walsh columns, R0 = T1 diag(sigma) T2 rounded to 2^-40, "
+                             "kappa(R0) ~ 1e4), m = 2^25, R = sqrt(m) R0"}
+    for n in NS:
+        Xt = Xs[n].T
+        ws = q.workspace(q.QL_AUTO, M, n, q.QL_F64, dev)
+        for meth in METHODS:
+            Rd, sd = _factor(q, meth, Xt, ws, q.QL_ARITH_DF)
+            R6, s6 = _factor(q, meth, Xt, ws, q.QL_ARITH_F64)
+            out["gauss"].append({"method": meth, "n": n, "df_vs_f64": rel_err(Rd, R6), "df_vs_f64_row": row_err(Rd, R6),
+                                 "status": [sd, s6]})
+        del ws
+    worst = 0.0
+    for n in NS:
+        Xt_, R_ex = synth.hadamard_exact_device(M, n, KAPPA, seed=9000 + n, device=dev)
+        Xt = Xt_.T
+        ws = q.workspace(q.QL_AUTO, M, n, q.QL_F64, dev)
+        for meth in METHODS:
+            Rd, sd = _factor(q, meth, Xt, ws, q.QL_ARITH_DF)
+            R6, s6 = _factor(q, meth, Xt, ws, q.QL_ARITH_F64)
+            ed, e6 = rel_err(Rd, R_ex), rel_err(R6, R_ex)
+            rd, r6 = row_err(Rd, R_ex), row_err(R6, R_ex)
+            ratio = ed / max(e6, 1e-17)
+            worst = max(worst, ratio)
+            out["exact"].append({"method": meth, "n": n, "err_default": ed, "err_f64": e6, "ratio": round(ratio, 3),
+                                 "row_err_default": rd, "row_err_f64": r6, "status": [sd, s6]})
+        del Xt_, Xt, ws
+        torch.cuda.empty_cache()
+    out["max_ratio_default_over_f64"] = round(worst, 3)
+    out["seconds"] = round(time.time() - t0, 1)
+    return out
 
 
 def run_scholqr3(q, lib, torch, dev, stream, reps=3):
@@ -883,7 +989,43 @@ def oracle_sample(seconds: float):
             total_s += s
             total_bytes += 8.0 * ms_rows * n
             parts.append(f"{meth} n={n} m={ms_rows}")
+    # least squares through the QR of [A b] (FP64- and FP32-stored A; the oracle computes in
+    # FP64 on the stored values, the bytes are those of the stored [A b])
+    ms_rows = int(max(256, min(LS_M, budget * flop_rate / (2.0 * (LS_N + 1) ** 2))))
+    A, b, _ = synth.lstsq_case(ms_rows, LS_N, 1e3, seed=4242)
+    for name, itemsize in (("lstsq_f64", 8.0), ("lstsq_f32", 4.0)):
+        Ai, bi = (A, b) if itemsize == 8.0 else (A.astype(np.float32), b.astype(np.float32))
+        t0 = time.perf_counter()
+        oracle.lstsq(Ai, bi)
+        s = time.perf_counter() - t0
+        total_s += s
+        total_bytes += itemsize * ms_rows * (LS_N + 1)
+        parts.append(f"{name} n={LS_N} m={ms_rows}")
     return total_bytes / total_s / 1e9, total_s, "; ".join(parts)
+
+
+def cpu_context(rows: int = 1 << 22):
+    """All host cores, LAPACK's Householder QR through torch.linalg.qr(mode='r') on a row
+    sample of every sweep width: a context number beside the single-thread oracle (a
+    baseline, not the target)."""
+    import torch
+
+    from paper_2603_20889_gb300 import synth
+
+    total_bytes, total_s, parts = 0.0, 0.0, []
+    for n in NS:
+        X = torch.from_numpy(synth.conditioned(rows, n, KAPPA, seed=1000 + n))
+        torch.linalg.qr(X[: 1 << 12], mode="r")  # warm-up
+        t0 = time.perf_counter()
+        torch.linalg.qr(X, mode="r")
+        s = time.perf_counter() - t0
+        total_s += s
+        total_bytes += 8.0 * rows * n
+        parts.append(f"n={n}: {s * 1e3:.1f} ms")
+        del X
+    return {"value": round(total_bytes / total_s / 1e9, 3), "unit": "GB/s", "cores": torch.get_num_threads(),
+            "kind": "torch.linalg.qr(mode='r') (LAPACK Householder), one call per n",
+            "sample": f"m = {rows} rows of the sweep's X for n in {NS} (TSQR-equivalent: one R per X); " + "; ".join(parts)}
 
 
 def cpu_baseline(seconds):
@@ -963,6 +1105,11 @@ def main():
     out = run_ours(args, rank, world, local_rank)
     if rank == 0:
         out["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+        if args.cpu_context:
+            try:
+                out["cpu_context"] = cpu_context()
+            except Exception as exc:
+                out["cpu_context"] = {"error": repr(exc)[:300]}
         print(json.dumps(out))
     if world > 1:
         import torch

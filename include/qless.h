@@ -82,6 +82,27 @@ const char* ql_version(void);
  * benchmarks: every launch of every entry point, gated fallback launches included). */
 uint64_t ql_launch_count(void);
 
+/*
+ * Measured compute-pipe throughput of the current device (measurement support for the
+ * roofline of the arithmetic-bound kernels; the paper has no counterpart).  Fills out[4]
+ * (host memory) with TFLOP/s: [0] FP32 FMA, [1] FP64 FMA, [2] FP64 tensor-core MMA
+ * (mma.sync m8n8k4), [3] the library's double-float multiply-accumulate in FP64-equivalent
+ * flops (2 per operation).  Synchronous: launches four timed kernels (a few tens of ms
+ * each) on `stream`, allocates and frees one small device buffer.  QL_ERR_ARG for a null
+ * out, QL_ERR_CUDA if a launch or the timing fails.
+ */
+ql_status ql_measure_peaks(double* out, void* stream);
+
+/*
+ * Self-check of the device-side failure reporting (test support; the paper has no
+ * counterpart).  One warp initialises an mbarrier and waits on it with the same bounded
+ * wait the tensor-core kernels use, giving up after limit_clocks (0 < limit <= 2^34) SM
+ * clocks.  arrive != 0: a thread arrives first and info = {QL_OK, 0}; arrive == 0: nothing
+ * arrives, the wait runs out and info = {QL_ERR_TIMEOUT, 1}.  Nothing asynchronous is in
+ * flight during the wait.  info: device int32[2] (required).  Asynchronous on stream.
+ */
+ql_status ql_check_bounded_wait(int32_t arrive, int64_t limit_clocks, int32_t* info, void* stream);
+
 /* Device workspace bytes for one call of `method` on an m x n problem of `dtype`
  * (QL_AUTO: the maximum over the methods).  0 on bad arguments. */
 size_t ql_workspace_bytes(ql_method method, int64_t m, int64_t n, ql_dtype dtype);

@@ -207,6 +207,21 @@ def rel_err(R, R_ref):
     return float(np.linalg.norm(R - R_ref) / (den if den > 0 else 1.0))
 
 
+def row_err(R, R_ref):
+    """max_ij |R_ij - R_ref_ij| / |R_ref_ii| over the upper triangle: the error of every
+    entry relative to its row's diagonal (rows whose reference diagonal is zero are scaled
+    by ||R_ref||_F).  A backward-stable R has |dR_ij| <= c u ||X|| <= c u kappa |R_ii|, so
+    the parity bound applies row by row; a wrong small last row, invisible in the
+    Frobenius ratio at large kappa, fails it."""
+    R = np.asarray(R, dtype=np.float64)
+    R_ref = np.asarray(R_ref, dtype=np.float64)
+    fro = float(np.linalg.norm(R_ref)) or 1.0
+    d = np.abs(np.diag(R_ref)).copy()
+    d[d == 0] = fro
+    D = np.triu(np.abs(R - R_ref)) / d[:, None]
+    return float(D.max()) if D.size else 0.0
+
+
 def tolerance(n, kappa):
     """Parity bound ||R - R_ref||_F / ||R_ref||_F <= 1e-13 * n * kappa(X)."""
     return 1e-13 * n * max(float(kappa), 1.0)

@@ -36,6 +36,8 @@ SIGNATURES = {
     "ql_set_arith": (_i32, [_i32]),
     "ql_version": (ctypes.c_char_p, []),
     "ql_launch_count": (ctypes.c_uint64, []),
+    "ql_measure_peaks": (_i32, [_vp, _vp]),
+    "ql_check_bounded_wait": (_i32, [_i32, _i64, _vp, _vp]),
     "ql_workspace_bytes": (_sz, [_i32, _i64, _i64, _i32]),
     "ql_tsqr_qless": (_i32, [_i64, _i64, _vp, _i32, _i64, _dp, _i64, _vp, _vp, _sz, _vp]),
     "ql_tsqr_qless_noalloc": (_i32, [_i64, _i64, _vp, _i32, _i64, _dp, _i64, _vp, _vp]),
@@ -161,6 +163,14 @@ def _colmajor(X):
         raise ValueError("X must be column-major: an (m, n) view with stride(0) == 1 (e.g. Xt.T)")
     ld = X.stride(1) if n > 1 else max(m, 1)
     return m, n, max(ld, max(m, 1)), dt
+
+
+def measure_peaks(stream=None) -> dict:
+    """Measured compute throughput of the current GPU in TFLOP/s (ql_measure_peaks)."""
+    out = (ctypes.c_double * 4)()
+    _check(load_library().ql_measure_peaks(ctypes.cast(out, ctypes.c_void_p), _stream_ptr(stream)),
+           "ql_measure_peaks")
+    return {"fp32_fma": out[0], "fp64_fma": out[1], "fp64_mma": out[2], "df_fma": out[3]}
 
 
 def set_arith(mode: int) -> int:

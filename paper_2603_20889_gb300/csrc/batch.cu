@@ -91,7 +91,7 @@ QL_DEV void batch_chunk(const BatchItem& it, int64_t chunk, unsigned char* smem,
   const int64_t t1 = min(it.tiles, t0 + it.tiles_per_chunk);
   cta.run(p, 0, t0, t1);
   const int n = it.n;
-  if (threadIdx.x == 0 && cta.out_of_range(n)) {
+  if (threadIdx.x == 0 && cta.out_of_range(n, it.m)) {
     atomicOr(&flags[it.flag_idx], 1);
     atomicOr(&flags[-1], 1);  // any_flag lives just before the per-problem flags
   }
@@ -103,7 +103,7 @@ QL_DEV void batch_chunk(const BatchItem& it, int64_t chunk, unsigned char* smem,
   double* slot = tv.slots + (size_t)chunk * n * n;
   for (int i = threadIdx.x; i < n * n; i += T) {
     int c = i / n, r = i % n;
-    __stcg(slot + i, r <= c ? Ar::to_double(cta.R[r * NC + c]) : 0.0);
+    __stcg(slot + i, r <= c ? Ar::r_to_double(cta.R[r * NC + c]) : 0.0);
   }
   double* Ra = cta.arena;
   double* Rb = cta.arena + NC * NC;

@@ -107,6 +107,28 @@ QL_DEV df df_split_double(double x, int& E) {
   return r;
 }
 
+// Triple-float ("tf"): value = hi + mid + lo, about 72 significant bits, built from the
+// same error-free transformations.  Used for values carried across many updates (the
+// running TSQR triangle), where double-float rounding would accumulate.
+struct tf {
+  float hi, mid, lo;
+};
+QL_DEV tf tf_neg(tf a) { return tf{-a.hi, -a.mid, -a.lo}; }
+QL_DEV df tf_to_df(tf a) { return df{a.hi, a.mid}; }
+QL_DEV double tf_to_double(tf a) { return ((double)a.hi + (double)a.mid) + (double)a.lo; }
+// a + b (tf + df): exact two-sums of the leading parts, the third-order terms (below
+// 2^-48 of the result) summed in FP32, then renormalised; error about 2^-72 |a + b|.
+QL_DEV tf tf_add_df(tf a, df b) {
+  float s0, e0, s1, e1, s2, e2, h, u, m, l;
+  two_sum(a.hi, b.hi, s0, e0);
+  two_sum(a.mid, b.lo, s1, e1);
+  two_sum(s1, e0, s2, e2);
+  const float t = __fadd_rn(__fadd_rn(e1, e2), a.lo);
+  two_sum(s0, s2, h, u);
+  two_sum(u, t, m, l);
+  return tf{h, m, l};
+}
+
 QL_DEV df shfl_xor(df a, int mask) {
   return df{__shfl_xor_sync(0xffffffffu, a.hi, mask), __shfl_xor_sync(0xffffffffu, a.lo, mask)};
 }
@@ -156,6 +178,15 @@ struct ArithDF {
   QL_DEV static double to_double(T a) { return df_to_double(a); }
   QL_DEV static T from_double(double x) { return df_from_double_rn(x); }
   QL_DEV static T shfl(T a, int mask) { return shfl_xor(a, mask); }
+  // Values carried across tiles (the running TSQR triangle): triple-float, so that their
+  // many small updates round at about 2^-72 instead of double-float's 2^-48.
+  using RT = tf;
+  QL_DEV static RT r_zero() { return tf{0.0f, 0.0f, 0.0f}; }
+  QL_DEV static T r_get(RT r) { return tf_to_df(r); }
+  QL_DEV static bool r_negative(RT r) { return r.hi < 0.0f; }
+  QL_DEV static RT r_neg(RT r) { return tf_neg(r); }
+  QL_DEV static RT r_add(RT r, T c) { return tf_add_df(r, c); }  // r + c
+  QL_DEV static double r_to_double(RT r) { return tf_to_double(r); }
 };
 
 struct ArithF64 {
@@ -188,6 +219,13 @@ struct ArithF64 {
   QL_DEV static double to_double(T a) { return a; }
   QL_DEV static T from_double(double x) { return x; }
   QL_DEV static T shfl(T a, int mask) { return __shfl_xor_sync(0xffffffffu, a, mask); }
+  using RT = double;
+  QL_DEV static RT r_zero() { return 0.0; }
+  QL_DEV static T r_get(RT r) { return r; }
+  QL_DEV static bool r_negative(RT r) { return r < 0.0; }
+  QL_DEV static RT r_neg(RT r) { return -r; }
+  QL_DEV static RT r_add(RT r, T c) { return r + c; }
+  QL_DEV static double r_to_double(RT r) { return r; }
 };
 
 // Range accepted by the double-float kernels: every nonzero block-column maximum |x| in
@@ -195,6 +233,16 @@ struct ArithF64 {
 // only used to detect columns whose block maximum is tiny.
 constexpr int kDfEmaxLimit = 1023 + 50;
 constexpr int kDfEminLimit = 1023 - 40;
+// Kernels whose double-float values include sums of squares over all m rows (column norms
+// and Gram entries, up to m max|x|^2) also need m 2^(2 (e + 1)) <= 2^124 for a biased
+// exponent limit 1023 + e: the upper limit drops by half a binade per doubling of m
+// (e = 48 at m = 2^25, 47 at m = 2^28) and stays at most 50.
+__host__ __device__ inline int df_emax_limit(int64_t m) {
+  int bits = 0;
+  while (bits < 62 && ((int64_t)1 << bits) < m) ++bits;  // ceil(log2 m)
+  const int e = (122 - bits) / 2;
+  return 1023 + (e < 50 ? e : 50);
+}
 
 // ---------------------------------------------------------------------------------------
 // cp.async staging (Ampere-style per-thread async copies; any element-aligned address).

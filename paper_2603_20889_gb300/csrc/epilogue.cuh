@@ -47,17 +47,30 @@ QL_DEV void write_info(int32_t* info, int status, int index) {
   }
 }
 
+// Status of a finished factorisation: a non-finite R first; otherwise a bounded wait that
+// gave up earlier in the call (the call was completed by the FP64 kernels, R is valid)
+// reports {QL_ERR_TIMEOUT, where}; otherwise QL_OK.
+QL_DEV void write_final_info(int32_t* info, bool nonfinite, int timeout_where) {
+  if (nonfinite)
+    write_info(info, QL_ERR_NONFINITE, 0);
+  else if (timeout_where)
+    write_info(info, QL_ERR_TIMEOUT, timeout_where);
+  else
+    write_info(info, QL_OK, 0);
+}
+
 // Root epilogue for a plain factorisation: R out, info.
 template <int T>
-QL_DEV void epilogue_r(double* Ra, int lds, int n, double* R, int64_t ldr, int32_t* info, int* s_flag) {
+QL_DEV void epilogue_r(double* Ra, int lds, int n, double* R, int64_t ldr, int32_t* info, int* s_flag,
+                       int timeout_where = 0) {
   bool bad = write_r_normalised<T>(Ra, lds, n, R, ldr, s_flag);
-  write_info(info, bad ? QL_ERR_NONFINITE : QL_OK, 0);
+  write_final_info(info, bad, timeout_where);
 }
 
 // Root epilogue for least squares: Ra holds R_ext (n1 x n1, n1 = n + 1).
 template <int T>
 QL_DEV void epilogue_lstsq(double* Ra, int lds, int n1, double* x, double* resnorm, double* Rext,
-                           int32_t* info, double* zz, int* s_flag) {
+                           int32_t* info, double* zz, int* s_flag, int timeout_where = 0) {
   int n = n1 - 1;
   bool bad = write_r_normalised<T>(Ra, lds, n1, Rext, n1, s_flag);
   // zero diagonal entry of R -> rank deficient: report the first one
@@ -87,7 +100,7 @@ QL_DEV void epilogue_lstsq(double* Ra, int lds, int n1, double* x, double* resno
     __syncthreads();
   }
   if (threadIdx.x == 0) *resnorm = Ra[n * lds + n];
-  write_info(info, bad ? QL_ERR_NONFINITE : QL_OK, 0);
+  write_final_info(info, bad, timeout_where);
 }
 
 }  // namespace ql

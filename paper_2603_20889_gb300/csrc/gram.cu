@@ -22,13 +22,16 @@ static size_t gram_layout(int n, GramWs* w, void* base) {
   const size_t head = 512;  // flags, counters and the first pass's column exponents
   const size_t keep = (size_t)3 * kMaxN * kMaxN * sizeof(double);
   const size_t parts = (size_t)device_sm_count() * kGramMaxCtasPerSm * nc * nc * sizeof(double);
+  // FP64 accumulators of the tcgen05 kernel (64 columns, one CTA per SM)
+  const size_t fbuf = nc == 64 ? (size_t)device_sm_count() * 64 * 128 * sizeof(double) : 0;
   if (w && base) {
     unsigned char* b = static_cast<unsigned char*>(base);
     w->flags = reinterpret_cast<int*>(b);
     w->keep = reinterpret_cast<double*>(b + head);
     w->partials = reinterpret_cast<double*>(b + head + keep);
+    w->fbuf = reinterpret_cast<double*>(b + head + keep + parts);
   }
-  return head + keep + parts;
+  return head + keep + parts + fbuf;
 }
 
 size_t gram_workspace_bytes(int n) {

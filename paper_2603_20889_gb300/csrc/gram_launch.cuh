@@ -14,12 +14,19 @@
 namespace ql {
 
 constexpr int kGramMaxCtasPerSm = 4;
+// The double-float Gram accumulators are moved into FP64 every kGramFlushTiles tiles (and
+// at the end), so that no double-float sum runs over more than a few thousand rows: the
+// rounding of the long running sums (which grows like the square root of their length)
+// happens in FP64, and the short double-float sums' errors are independent from one flush
+// to the next.
+constexpr int kGramFlushTiles = 16;
 
 struct GramWs {
   int* flags;        // [0] range, [1] first-pass breakdown, [2] arrival counter pass 1, [3] pass 2,
                     // [64 + c]: largest biased exponent of column c over all rows (tensor-core pass 1)
   double* keep;      // 3 n x n blocks carried from pass 1 to pass 2 (row-major, ld n)
   double* partials;  // one NC x NC partial Gram per CTA
+  double* fbuf;      // tcgen05 kernel: FP64 accumulators per CTA, [NC columns][128 TMEM lanes]
 };
 
 template <typename S>
@@ -109,10 +116,14 @@ __global__ void __launch_bounds__(GramShape<NC>::T, 1) gram_kernel(GramArgs<S> a
   const bool useful = active && p0 < n && q0 < n;
 
   Acc acc[BS][BS];
+  double acc64[BS][BS];  // FP64 level of the double-float sums (stays zero in FP64 arithmetic)
 #pragma unroll
   for (int i = 0; i < BS; ++i)
 #pragma unroll
-    for (int j = 0; j < BS; ++j) acc[i][j] = Ar::acc_zero();
+    for (int j = 0; j < BS; ++j) {
+      acc[i][j] = Ar::acc_zero();
+      acc64[i][j] = 0.0;
+    }
 
   const int k = gridDim.x, bid = blockIdx.x;
   const int64_t t0 = a.tiles * bid / k, t1 = a.tiles * (bid + 1) / k;
@@ -178,23 +189,35 @@ __global__ void __launch_bounds__(GramShape<NC>::T, 1) gram_kernel(GramArgs<S> a
           for (int j = 0; j < BS; ++j) Ar::acc_fma(acc[i][j], yp[i], yq[j]);
       }
     }
+    if constexpr (!std::is_same<Acc, double>::value) {
+      if ((t - t0) % kGramFlushTiles == kGramFlushTiles - 1) {
+#pragma unroll
+        for (int i = 0; i < BS; ++i)
+#pragma unroll
+          for (int j = 0; j < BS; ++j) {
+            acc64[i][j] += Ar::to_double(Ar::acc_get(acc[i][j]));
+            acc[i][j] = Ar::acc_zero();
+          }
+      }
+    }
   }
   __syncthreads();
 
-  // reduce the row slices: red[(slice * NBT + blk) * BS * BS + i * BS + j]
-  V* red = Y0;
+  // reduce the row slices in FP64: red[(slice * NBT + blk) * BS * BS + i * BS + j]
+  double* red = reinterpret_cast<double*>(Y0);
   if (active) {
 #pragma unroll
     for (int i = 0; i < BS; ++i)
 #pragma unroll
-      for (int j = 0; j < BS; ++j) red[(slice * NBT + blk) * BS * BS + i * BS + j] = Ar::acc_get(acc[i][j]);
+      for (int j = 0; j < BS; ++j)
+        red[(slice * NBT + blk) * BS * BS + i * BS + j] = acc64[i][j] + Ar::to_double(Ar::acc_get(acc[i][j]));
   }
   __syncthreads();
   double* part = a.w.partials + (size_t)bid * NC * NC;
   for (int e = tid; e < NBT * BS * BS; e += T) {
     int b = e / (BS * BS), ij = e % (BS * BS);
-    V s = red[b * BS * BS + ij];
-    for (int sl = 1; sl < SL; ++sl) s = Ar::add(s, red[(sl * NBT + b) * BS * BS + ij]);
+    double s = red[b * BS * BS + ij];
+    for (int sl = 1; sl < SL; ++sl) s += red[(sl * NBT + b) * BS * BS + ij];
     int rem = b, pp = 0;
     while (rem >= Sh::NB - pp) {
       rem -= Sh::NB - pp;
@@ -202,7 +225,7 @@ __global__ void __launch_bounds__(GramShape<NC>::T, 1) gram_kernel(GramArgs<S> a
     }
     int qq = pp + rem;
     int p = pp * BS + ij / BS, q = qq * BS + ij % BS;
-    __stcg(part + p * NC + q, Ar::to_double(s));
+    __stcg(part + p * NC + q, s);
   }
   gram_finish<NC, T, S, Ar>(a, smem, colmax, misc);
 }
@@ -217,9 +240,10 @@ QL_DEV void gram_finish(const GramArgs<S>& a, unsigned char* smem, const int* co
   if (tid == 0) {
     bool bad = false;
     if constexpr (Ar::kRangeChecked) {
+      const int emax = df_emax_limit(a.m);  // Gram entries reach m max|x|^2
       for (int c = 0; c < n; ++c) {
         int e = colmax[c];
-        if (e != 0 && (e < kDfEminLimit || e > kDfEmaxLimit)) bad = true;
+        if (e != 0 && (e < kDfEminLimit || e > emax)) bad = true;
       }
     }
     if (bad) atomicOr(&a.w.flags[0], 1);
@@ -248,15 +272,12 @@ QL_DEV void gram_finish(const GramArgs<S>& a, unsigned char* smem, const int* co
   double* vec = Qs + NC * LE;  // 8 LE doubles
   int* sflag = reinterpret_cast<int*>(vec + 8 * LE);
   __syncthreads();
+  // fixed-order FP64 sum of the CTA partials (bitwise reproducible)
   for (int e = tid; e < n * n; e += T) {
     int p = e / n, q = e % n;
     if (p > q) continue;
-    V s = Ar::zero();
-    for (int b = 0; b < k; ++b) {
-      int E;
-      s = Ar::add(s, Ar::load(__ldcg(a.w.partials + (size_t)b * NC * NC + p * NC + q), E));
-    }
-    double v = Ar::to_double(s);
+    double v = 0.0;
+    for (int b = 0; b < k; ++b) v += __ldcg(a.w.partials + (size_t)b * NC * NC + p * NC + q);
     Cs[p * LE + q] = v;
     Cs[q * LE + p] = v;
   }
@@ -336,10 +357,13 @@ QL_DEV void gram_finish(const GramArgs<S>& a, unsigned char* smem, const int* co
     __syncthreads();
     householder_square<T>(Ps, LE, n, vec);
   }
+  // a bounded wait of the double-float launches that gave up (flags[4] = where) is reported
+  // by the FP64 launches that completed the call
+  const int tmo = *(volatile int*)&a.w.flags[4];
   if (a.epilogue == kEpiR)
-    epilogue_r<T>(Ps, LE, n, a.R, a.ldr, a.info, sflag);
+    epilogue_r<T>(Ps, LE, n, a.R, a.ldr, a.info, sflag, tmo);
   else
-    epilogue_lstsq<T>(Ps, LE, n, a.x, a.resnorm, a.Rext, a.info, vec, sflag);
+    epilogue_lstsq<T>(Ps, LE, n, a.x, a.resnorm, a.Rext, a.info, vec, sflag, tmo);
 }
 
 
@@ -389,7 +413,7 @@ __global__ void __launch_bounds__(256, 1) gram_tc_kernel(GramArgs<S> a) {
   const int rpart = (NC == 64) ? 0 : warp % WPC;
   const int ksw = XF == kXUpper ? (cbw >> 1) + 1 : KSTEPS;
   unsigned bq[XF != kXNone ? KSTEPS : 1][7][2];
-  float ysc[2][7];  // 2^(f_j - 7(d + 2)) for this thread's two Y columns and the 7 weights
+  float ysc[2][7];  // 2^(f_j - 12 - 7d) for this thread's two Y columns and the 7 weights
   if constexpr (XF != kXNone) {
     const double* M = a.w.keep + (size_t)n * n;  // pass-1 output, row-major, ld n
     const int jb = cbw * 8 + g;
@@ -412,17 +436,13 @@ __global__ void __launch_bounds__(256, 1) gram_tc_kernel(GramArgs<S> a) {
     F = max(F, __shfl_xor_sync(0xffffffffu, F, 2));  // max over column jb of M'
 #pragma unroll
     for (int ks = 0; ks < KSTEPS; ++ks) {
-      unsigned long long N[4];
-      unsigned sg[4];
+      long long Nb[4];
 #pragma unroll
-      for (int h = 0; h < 4; ++h) N[h] = fixed_of_double(mv[ks][h], F, sg[h]);
+      for (int h = 0; h < 4; ++h) Nb[h] = fixed48_of_double(mv[ks][h], F) + kDigitBias;
 #pragma unroll
       for (int q = 0; q < 7; ++q) {
-        const int sh = 7 * (6 - q);
-        bq[ks][q][0] = bf16_digit((unsigned)(N[0] >> sh) & 127u, sg[0]) |
-                       (bf16_digit((unsigned)(N[1] >> sh) & 127u, sg[1]) << 16);
-        bq[ks][q][1] = bf16_digit((unsigned)(N[2] >> sh) & 127u, sg[2]) |
-                       (bf16_digit((unsigned)(N[3] >> sh) & 127u, sg[3]) << 16);
+        bq[ks][q][0] = bf16x2_of_ints(balanced_digit_rt(Nb[0], q), balanced_digit_rt(Nb[1], q));
+        bq[ks][q][1] = bf16x2_of_ints(balanced_digit_rt(Nb[2], q), balanced_digit_rt(Nb[3], q));
       }
     }
     // the flush scale of this thread's Y columns cbw*8 + 2 t4 + h must stay a normal float
@@ -434,7 +454,7 @@ __global__ void __launch_bounds__(256, 1) gram_tc_kernel(GramArgs<S> a) {
       if (Fj > 0 && (f < -70 || f > 100)) bad = true;
 #pragma unroll
       for (int d = 0; d < 7; ++d) {
-        const int e = f - 7 * (d + 2);
+        const int e = f - kDigitScaleLog2 - 7 * d;
         ysc[h][d] = (Fj > 0 && !bad) ? __int_as_float((e + 127) << 23) : 0.0f;
       }
     }
@@ -445,13 +465,17 @@ __global__ void __launch_bounds__(256, 1) gram_tc_kernel(GramArgs<S> a) {
     }
   }
 
-  df acc[U][G][4];  // persistent per-unit C accumulators
+  df acc[U][G][4];        // per-unit C accumulators over the last few tiles
+  double acc64[U][G][4];  // and their FP64 level
 #pragma unroll
   for (int ui = 0; ui < U; ++ui)
 #pragma unroll
     for (int gi = 0; gi < G; ++gi)
 #pragma unroll
-      for (int e = 0; e < 4; ++e) acc[ui][gi][e] = df{0.0f, 0.0f};
+      for (int e = 0; e < 4; ++e) {
+        acc[ui][gi][e] = df{0.0f, 0.0f};
+        acc64[ui][gi][e] = 0.0;
+      }
 
   const int k = gridDim.x, bid = blockIdx.x;
   const int64_t t0 = a.tiles * bid / k, t1 = a.tiles * (bid + 1) / k;
@@ -475,25 +499,19 @@ __global__ void __launch_bounds__(256, 1) gram_tc_kernel(GramArgs<S> a) {
     for (int k2 = 0; k2 < PAIRS; ++k2) {
       const int pi = tid + T * k2, c = (2 * pi) / KT, r = (2 * pi) % KT;
       const int em = ex[c];
-      unsigned long long N[2];
-      unsigned sg[2];
+      long long Nb[2];
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         if constexpr (sizeof(S) == 8) {
-          N[h] = fixed_of_double((double)stage[c * KT + r + h], em, sg[h]);
+          Nb[h] = (em > 0 ? fixed48_of_double((double)stage[c * KT + r + h], em) : 0ll) + kDigitBias;
         } else {
-          float x = (float)stage[c * KT + r + h];
-          sg[h] = __float_as_uint(x) & 0x80000000u;
-          N[h] = em > 0 ? fixed_of_float(x, em - 896) : 0ull;
+          Nb[h] = (em > 0 ? fixed48_of_float((float)stage[c * KT + r + h], em - 896) : 0ll) + kDigitBias;
         }
       }
 #pragma unroll
-      for (int p = 0; p < Sh::ND; ++p) {
-        const int sh = 7 * (Sh::ND - 1 - p);
-        unsigned lo16 = bf16_digit((unsigned)(N[0] >> sh) & 127u, sg[0]);
-        unsigned hi16 = bf16_digit((unsigned)(N[1] >> sh) & 127u, sg[1]);
-        *reinterpret_cast<unsigned*>(slices + ((size_t)p * NC + c) * LDR + r) = lo16 | (hi16 << 16);
-      }
+      for (int p = 0; p < Sh::ND; ++p)
+        *reinterpret_cast<unsigned*>(slices + ((size_t)p * NC + c) * LDR + r) =
+            bf16x2_of_ints(balanced_digit_rt(Nb[0], p), balanced_digit_rt(Nb[1], p));
     }
   };
 
@@ -598,24 +616,16 @@ __global__ void __launch_bounds__(256, 1) gram_tc_kernel(GramArgs<S> a) {
       for (int k2 = 0; k2 < PAIRS; ++k2) {
         const int pi = tid + T * k2, c = (2 * pi) / KT, r = (2 * pi) % KT;
         const int em = expo[c];
-        unsigned long long N[2];
-        unsigned sg[2];
+        long long Nb[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const df y = ydf[c * LDY + r + h];
-          sg[h] = __float_as_uint(y.hi) & 0x80000000u;
-          unsigned long long nh = fixed_of_float(y.hi, em);
-          unsigned long long nl = fixed_of_float(y.lo, em);
-          bool same = ((__float_as_uint(y.lo) ^ __float_as_uint(y.hi)) & 0x80000000u) == 0u;
-          N[h] = same ? nh + nl : (nh > nl ? nh - nl : 0ull);
+          Nb[h] = fixed48_of_float(y.hi, em) + fixed48_of_float(y.lo, em) + kDigitBias;
         }
 #pragma unroll
-        for (int p = 0; p < Sh::ND; ++p) {
-          const int sh = 7 * (Sh::ND - 1 - p);
-          unsigned lo16 = bf16_digit((unsigned)(N[0] >> sh) & 127u, sg[0]);
-          unsigned hi16 = bf16_digit((unsigned)(N[1] >> sh) & 127u, sg[1]);
-          *reinterpret_cast<unsigned*>(slices + ((size_t)p * NC + c) * LDR + r) = lo16 | (hi16 << 16);
-        }
+        for (int p = 0; p < Sh::ND; ++p)
+          *reinterpret_cast<unsigned*>(slices + ((size_t)p * NC + c) * LDR + r) =
+              bf16x2_of_ints(balanced_digit_rt(Nb[0], p), balanced_digit_rt(Nb[1], p));
       }
     }
     __syncthreads();
@@ -663,18 +673,40 @@ __global__ void __launch_bounds__(256, 1) gram_tc_kernel(GramArgs<S> a) {
               mma_bf16(accd[p + q][gi], af[p][0], af[p][1], af[p][2], af[p][3], bf[q][0], bf[q][1]);
         }
       }
+      // fold the seven weights of each entry (weights 6..3 in FP32, together below 2^-21 of
+      // the leading one; 2..0 with exact two-sums), scale by 2^(e_i + e_j) and add once
 #pragma unroll
       for (int gi = 0; gi < G; ++gi) {
         const float fj0 = pow2c[(cb0 + gi) * 8 + 2 * t4], fj1 = pow2c[(cb0 + gi) * 8 + 2 * t4 + 1];
+        const float f4[4] = {fi0 * fj0, fi0 * fj1, fi1 * fj0, fi1 * fj1};
 #pragma unroll
-        for (int dd = 0; dd < 7; ++dd) {
-          const float sd = __int_as_float((127 - 7 * (dd + 2)) << 23);  // 2^(-7d)
-          acc[ui][gi][0] = df_add(acc[ui][gi][0], df{accd[dd][gi][0] * (fi0 * fj0 * sd), 0.0f});
-          acc[ui][gi][1] = df_add(acc[ui][gi][1], df{accd[dd][gi][1] * (fi0 * fj1 * sd), 0.0f});
-          acc[ui][gi][2] = df_add(acc[ui][gi][2], df{accd[dd][gi][2] * (fi1 * fj0 * sd), 0.0f});
-          acc[ui][gi][3] = df_add(acc[ui][gi][3], df{accd[dd][gi][3] * (fi1 * fj1 * sd), 0.0f});
+        for (int e = 0; e < 4; ++e) {
+          float hi = accd[6][gi][e] * __int_as_float((127 - kDigitScaleLog2 - 42) << 23);
+#pragma unroll
+          for (int dd = 5; dd >= 3; --dd)
+            hi = __fmaf_rn(accd[dd][gi][e], __int_as_float((127 - kDigitScaleLog2 - 7 * dd) << 23), hi);
+          float lo = 0.0f;
+#pragma unroll
+          for (int dd = 2; dd >= 0; --dd) {
+            float s2, e2;
+            two_sum(hi, accd[dd][gi][e] * __int_as_float((127 - kDigitScaleLog2 - 7 * dd) << 23), s2, e2);
+            hi = s2;
+            lo = __fadd_rn(lo, e2);
+          }
+          acc[ui][gi][e] = df_add(acc[ui][gi][e], df{hi * f4[e], lo * f4[e]});
         }
       }
+    }
+    if ((t - t0) % kGramFlushTiles == kGramFlushTiles - 1) {  // double-float sums -> FP64
+#pragma unroll
+      for (int ui = 0; ui < U; ++ui)
+#pragma unroll
+        for (int gi = 0; gi < G; ++gi)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            acc64[ui][gi][e] += df_to_double(acc[ui][gi][e]);
+            acc[ui][gi][e] = df{0.0f, 0.0f};
+          }
     }
   }
   __syncthreads();
@@ -682,23 +714,24 @@ __global__ void __launch_bounds__(256, 1) gram_tc_kernel(GramArgs<S> a) {
     for (int c = tid; c < n; c += T)
       if (colmax[c] > 0) atomicMax(&a.w.flags[64 + c], colmax[c]);
   }
-  // combine the row parts of each C tile and store this CTA's partial Gram matrix
-  df* red = reinterpret_cast<df*>(smem + Sm::kOffSlices);  // [unit][G][4][32]
+  // combine the row parts of each C tile (FP64) and store this CTA's partial Gram matrix
+  double* red = reinterpret_cast<double*>(smem + Sm::kOffSlices);  // [unit][G][4][32]
 #pragma unroll
   for (int ui = 0; ui < U; ++ui)
 #pragma unroll
     for (int gi = 0; gi < G; ++gi)
 #pragma unroll
-      for (int e = 0; e < 4; ++e) red[(((warp * U + ui) * G + gi) * 4 + e) * 32 + lane] = acc[ui][gi][e];
+      for (int e = 0; e < 4; ++e)
+        red[(((warp * U + ui) * G + gi) * 4 + e) * 32 + lane] = acc64[ui][gi][e] + df_to_double(acc[ui][gi][e]);
   __syncthreads();
   double* part = a.w.partials + (size_t)bid * NC * NC;
   for (int idx = tid; idx < Sh::GROUPS * G * 4 * 32; idx += T) {
     const int ln = idx % 32, e = (idx / 32) % 4, gi = (idx / 128) % G, gr = idx / (128 * G);
-    df s = df{0.0f, 0.0f};
-    for (int kq = 0; kq < KS; ++kq) s = df_add(s, red[(((gr * KS + kq) * G + gi) * 4 + e) * 32 + ln]);
+    double s = 0.0;
+    for (int kq = 0; kq < KS; ++kq) s += red[(((gr * KS + kq) * G + gi) * 4 + e) * 32 + ln];
     const int rb2 = gr / GPR, cbb = (gr % GPR) * G + gi;
     const int i = rb2 * 16 + (ln >> 2) + (e >= 2 ? 8 : 0), j = cbb * 8 + 2 * (ln & 3) + (e & 1);
-    if (i < NC && j < NC) __stcg(part + i * NC + j, df_to_double(s));
+    if (i < NC && j < NC) __stcg(part + i * NC + j, s);
   }
   gram_finish<NC, T, S, ArithDF>(a, smem, colmax, misc);
 }
@@ -806,7 +839,7 @@ __global__ void __launch_bounds__(umma_threads<XF>(), 1) gram_umma_kernel(GramAr
   const int rpart = (NC == 64) ? 0 : warp % WPC;
   const int ksw = XF == kXUpper ? (cbw >> 1) + 1 : KSTEPS;
   unsigned bq[XF != kXNone ? KSTEPS : 1][7][2];
-  float ysc[2][7];  // 2^(f_j - 7(d + 2)) for this thread's two Y columns and the 7 weights
+  float ysc[2][7];  // 2^(f_j - 12 - 7d) for this thread's two Y columns and the 7 weights
   if constexpr (XF != kXNone) {
     const double* M = a.w.keep + (size_t)n * n;  // pass-1 output, row-major, ld n
     const int jb = cbw * 8 + g;
@@ -829,17 +862,13 @@ __global__ void __launch_bounds__(umma_threads<XF>(), 1) gram_umma_kernel(GramAr
     F = max(F, __shfl_xor_sync(0xffffffffu, F, 2));  // max over column jb of M'
 #pragma unroll
     for (int ks = 0; ks < KSTEPS; ++ks) {
-      unsigned long long N[4];
-      unsigned sg[4];
+      long long Nb[4];
 #pragma unroll
-      for (int h = 0; h < 4; ++h) N[h] = fixed_of_double(mv[ks][h], F, sg[h]);
+      for (int h = 0; h < 4; ++h) Nb[h] = fixed48_of_double(mv[ks][h], F) + kDigitBias;
 #pragma unroll
       for (int q = 0; q < 7; ++q) {
-        const int sh = 7 * (6 - q);
-        bq[ks][q][0] = bf16_digit((unsigned)(N[0] >> sh) & 127u, sg[0]) |
-                       (bf16_digit((unsigned)(N[1] >> sh) & 127u, sg[1]) << 16);
-        bq[ks][q][1] = bf16_digit((unsigned)(N[2] >> sh) & 127u, sg[2]) |
-                       (bf16_digit((unsigned)(N[3] >> sh) & 127u, sg[3]) << 16);
+        bq[ks][q][0] = bf16x2_of_ints(balanced_digit_rt(Nb[0], q), balanced_digit_rt(Nb[1], q));
+        bq[ks][q][1] = bf16x2_of_ints(balanced_digit_rt(Nb[2], q), balanced_digit_rt(Nb[3], q));
       }
     }
     bool bad = false;
@@ -850,7 +879,7 @@ __global__ void __launch_bounds__(umma_threads<XF>(), 1) gram_umma_kernel(GramAr
       if (Fj > 0 && (f < -70 || f > 100)) bad = true;
 #pragma unroll
       for (int d = 0; d < 7; ++d) {
-        const int e = f - 7 * (d + 2);
+        const int e = f - kDigitScaleLog2 - 7 * d;
         ysc[h][d] = (Fj > 0 && !bad) ? __int_as_float((e + 127) << 23) : 0.0f;
       }
     }
@@ -875,8 +904,14 @@ __global__ void __launch_bounds__(umma_threads<XF>(), 1) gram_umma_kernel(GramAr
   const int qd = warp & 3, hh = warp >> 2;  // TMEM lane quarter and column part of this warp
   const int L = 32 * qd + lane, kq = L / NC, li = L % NC;
   df acc[HALF];
+  // FP64 level of the accumulators: this CTA's [NC columns][128 lanes] block of the
+  // workspace (L2-resident; each thread touches only its own entries)
+  double* fb = a.w.fbuf + (size_t)blockIdx.x * NC * 128;
 #pragma unroll
-  for (int j = 0; j < HALF; ++j) acc[j] = df{0.0f, 0.0f};
+  for (int j = 0; j < HALF; ++j) {
+    acc[j] = df{0.0f, 0.0f};
+    __stcg(fb + (size_t)(hh * HALF + j) * 128 + L, 0.0);
+  }
 
   const int k = gridDim.x, bid = blockIdx.x;
   const int64_t t0 = a.tiles * bid / k, t1 = a.tiles * (bid + 1) / k;
@@ -913,20 +948,14 @@ __global__ void __launch_bounds__(umma_threads<XF>(), 1) gram_umma_kernel(GramAr
     lphase ^= 1u;
     return landed;
   };
-  // seven signed base-128 digits per value into the core-matrix layout: a warp writes one
+  // seven balanced base-128 digits per value into the core-matrix layout: a warp writes one
   // 8 x 8 core matrix (128 contiguous bytes) per step, a lane two rows of one column
-  auto put_digits = [&](int c, int r, unsigned long long N0, unsigned s0, unsigned long long N1, unsigned s1) {
+  auto put_digits = [&](int c, int r, long long Nb0, long long Nb1) {
     unsigned char* base = digits + (c >> 3) * SBO + (r >> 3) * LBO + (c & 7) * 16 + (r & 7) * 2;
-    const unsigned sgn = (s0 >> 16) | s1;  // the sign bits of both bf16 halves
 #pragma unroll
-    for (int p = 0; p < Sh::ND; ++p) {
-      const int sh = 7 * (Sh::ND - 1 - p);
-      // d -> float exactly as (2^23 + d) - 2^23; the upper halves of the two floats are the
-      // bf16 digits, packed with one byte permute
-      const float f0 = __fsub_rn(__uint_as_float(0x4B000000u | ((unsigned)(N0 >> sh) & 127u)), 8388608.0f);
-      const float f1 = __fsub_rn(__uint_as_float(0x4B000000u | ((unsigned)(N1 >> sh) & 127u)), 8388608.0f);
-      *reinterpret_cast<unsigned*>(base + p * PLANE) = __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632) | sgn;
-    }
+    for (int p = 0; p < Sh::ND; ++p)
+      *reinterpret_cast<unsigned*>(base + p * PLANE) =
+          bf16x2_of_ints(balanced_digit_rt(Nb0, p), balanced_digit_rt(Nb1, p));
   };
   // the staged X, ex[c] the biased double exponent that bounds column c
   auto slice_stage = [&](const int* ex) {
@@ -934,30 +963,28 @@ __global__ void __launch_bounds__(umma_threads<XF>(), 1) gram_umma_kernel(GramAr
     for (int k2 = 0; k2 < PAIRS; ++k2) {
       const int cm = warp + NW * k2, c = 8 * (cm / CPG) + (lane >> 2), r = 8 * (cm % CPG) + 2 * (lane & 3);
       const int em = c < n ? ex[c] : 0;  // columns past n are zero (a bulk-loaded stage holds stale data there)
-      unsigned long long N[2];
-      unsigned sg[2];
+      long long Nb[2];
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         if constexpr (sizeof(S) == 8) {
-          const double x = em > 0 ? (double)stage[c * LDS + r + h] : 0.0;
-          N[h] = fixed_of_double(x, em, sg[h]);
+          Nb[h] = (em > 0 ? fixed48_of_double((double)stage[c * LDS + r + h], em) : 0ll) + kDigitBias;
         } else {
-          float x = em > 0 ? (float)stage[c * LDS + r + h] : 0.0f;
-          sg[h] = __float_as_uint(x) & 0x80000000u;
-          N[h] = em > 0 ? fixed_of_float(x, em - 896) : 0ull;
+          Nb[h] = (em > 0 ? fixed48_of_float((float)stage[c * LDS + r + h], em - 896) : 0ll) + kDigitBias;
         }
       }
-      put_digits(c, r, N[0], sg[0], N[1], sg[1]);
+      put_digits(c, r, Nb[0], Nb[1]);
     }
   };
 
   bool ok = true;
+  int fail_where = 0;  // 1: a tile copy never completed, 2: the MMAs never completed
   if (t0 < t1) issue(t0);
   __syncthreads();
   uint32_t phase = 0;
   for (int64_t t = t0; t < t1; ++t) {
     if (!__syncthreads_and(wait_tile(t))) {  // the copy engine did not deliver: FP64 redoes the call
       ok = false;
+      fail_where = 1;
       break;
     }
     for (int i = tid; i < NC; i += T) expo[i] = 0;
@@ -1056,18 +1083,13 @@ __global__ void __launch_bounds__(umma_threads<XF>(), 1) gram_umma_kernel(GramAr
       for (int k2 = 0; k2 < PAIRS; ++k2) {
         const int cm = warp + NW * k2, c = 8 * (cm / CPG) + (lane >> 2), r = 8 * (cm % CPG) + 2 * (lane & 3);
         const int em = expo[c];
-        unsigned long long N[2];
-        unsigned sg[2];
+        long long Nb[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const df y = ydf[c * LDY + r + h];
-          sg[h] = __float_as_uint(y.hi) & 0x80000000u;
-          unsigned long long nh = fixed_of_float(y.hi, em);
-          unsigned long long nl = fixed_of_float(y.lo, em);
-          bool same = ((__float_as_uint(y.lo) ^ __float_as_uint(y.hi)) & 0x80000000u) == 0u;
-          N[h] = same ? nh + nl : (nh > nl ? nh - nl : 0ull);
+          Nb[h] = fixed48_of_float(y.hi, em) + fixed48_of_float(y.lo, em) + kDigitBias;
         }
-        put_digits(c, r, N[0], sg[0], N[1], sg[1]);
+        put_digits(c, r, Nb[0], Nb[1]);
       }
     }
     fence_proxy_async_smem();  // the digit planes are read by the tensor core
@@ -1096,6 +1118,7 @@ __global__ void __launch_bounds__(umma_threads<XF>(), 1) gram_umma_kernel(GramAr
     if (!__syncthreads_and(done)) {  // the tensor core did not finish: let FP64 redo the call
       if (t + 1 < t1) wait_tile(t + 1);  // no copy may still be writing when the CTA moves on
       ok = false;
+      fail_where = 2;
       break;
     }
     tc_fence_after();
@@ -1110,7 +1133,7 @@ __global__ void __launch_bounds__(umma_threads<XF>(), 1) gram_umma_kernel(GramAr
       uint32_t vm[7];  // lanes beyond the truncation may hold non-finite products of "plane 7": masked, not scaled
 #pragma unroll
       for (int tb = 0; tb < 7; ++tb) {
-        sw[tb] = tb + kq <= 6 ? fi * __int_as_float((127 - 7 * (tb + kq + 2)) << 23) : 0.0f;
+        sw[tb] = tb + kq <= 6 ? fi * __int_as_float((127 - kDigitScaleLog2 - 7 * (tb + kq)) << 23) : 0.0f;
         vm[tb] = tb + kq <= 6 ? 0xffffffffu : 0u;
       }
       const uint32_t lane_base = tbase + ((uint32_t)(32 * qd) << 16) + (uint32_t)(hh * HALF);
@@ -1139,29 +1162,41 @@ __global__ void __launch_bounds__(umma_threads<XF>(), 1) gram_umma_kernel(GramAr
         }
       }
     }
+    if ((t - t0) % kGramFlushTiles == kGramFlushTiles - 1) {  // double-float sums -> FP64 (L2)
+#pragma unroll
+      for (int j = 0; j < HALF; ++j) {
+        double* f = fb + (size_t)(hh * HALF + j) * 128 + L;
+        __stcg(f, __ldcg(f) + df_to_double(acc[j]));
+        acc[j] = df{0.0f, 0.0f};
+      }
+    }
     tc_fence_before();
   }
   cp_async_wait_all();  // an early exit may leave a prefetch in flight
   tc_fence_before();
   __syncthreads();
   if (warp == 0) tmem_dealloc(tbase, Sh::TCOLS);
-  if (!ok && tid == 0) atomicOr(&a.w.flags[0], 2);
+  if (!ok && tid == 0) {  // the FP64 launches redo the call and report {QL_ERR_TIMEOUT, where}
+    atomicCAS(&a.w.flags[4], 0, fail_where);
+    atomicOr(&a.w.flags[0], 2);
+  }
   if constexpr (XF == kXNone) {  // column exponents of the whole matrix, for the second pass
     for (int c = tid; c < n; c += T)
       if (colmax[c] > 0) atomicMax(&a.w.flags[64 + c], colmax[c]);
   }
-  // combine the plane offsets of each entry and store this CTA's partial Gram matrix
-  df* red = reinterpret_cast<df*>(smem + Sm::kOffStage);  // [lane L][column]
+  // combine the plane offsets of each entry (FP64) and store this CTA's partial Gram matrix
+  double* red = reinterpret_cast<double*>(smem + Sm::kOffStage);  // [lane L][column]
 #pragma unroll
-  for (int j = 0; j < HALF; ++j) red[L * NC + hh * HALF + j] = acc[j];
+  for (int j = 0; j < HALF; ++j)
+    red[L * NC + hh * HALF + j] = __ldcg(fb + (size_t)(hh * HALF + j) * 128 + L) + df_to_double(acc[j]);
   __syncthreads();
   double* part = a.w.partials + (size_t)bid * NC * NC;
   for (int e = tid; e < NC * NC; e += T) {
     const int i = e / NC, j = e % NC;
-    df s = df{0.0f, 0.0f};
+    double s = 0.0;
 #pragma unroll
-    for (int kk = 0; kk < SP; ++kk) s = df_add(s, red[(kk * NC + i) * NC + j]);
-    __stcg(part + e, df_to_double(s));
+    for (int kk = 0; kk < SP; ++kk) s += red[(kk * NC + i) * NC + j];
+    __stcg(part + e, s);
   }
   gram_finish<NC, T, S, ArithDF>(a, smem, colmax, misc);
 }

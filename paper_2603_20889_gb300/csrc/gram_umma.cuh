@@ -115,12 +115,17 @@ QL_DEV bool mbar_try_wait(uint64_t* mbar, uint32_t parity) {
       : "memory");
   return done != 0;
 }
-// Wait for the phase with the given parity; gives up after about 2^32 clocks (2 s).
-QL_DEV bool mbar_wait_bounded(uint64_t* mbar, uint32_t parity) {
+// Wait for the phase with the given parity; gives up after `limit` clocks (default 2^32,
+// about 2 s) and returns false.
+QL_DEV bool mbar_wait_bounded(uint64_t* mbar, uint32_t parity, long long limit = 1ll << 32) {
   const long long t0 = clock64();
   while (!mbar_try_wait(mbar, parity))
-    if (clock64() - t0 > (1ll << 32)) return false;
+    if (clock64() - t0 > limit) return false;
   return true;
+}
+QL_DEV void mbar_arrive(uint64_t* mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];
+" ::"r"(smem_addr(mbar)) : "memory");
 }
 QL_DEV void mbar_arrive_expect_tx(uint64_t* mbar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(mbar)), "r"(bytes)

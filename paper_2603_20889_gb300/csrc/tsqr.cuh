@@ -14,6 +14,19 @@
 // for x = [R_jj; W(:,j)] and beta = -sign(R_jj) ||x||, v = x - beta e_1, the reflector
 // H = I - v v^T / (-beta v_1) (v_1 = R_jj - beta) updates column c > j by
 //   f_c = (W(:,j)^T W(:,c) + v_1 R_jc) / (-beta v_1),   R_jc -= v_1 f_c,   W(:,c) -= W(:,j) f_c.
+//
+// Precision.  The running triangle R is carried across the CTA's tiles in triple-float
+// (double-float policy) or FP64.  With a = |R_jj|, b = |beta| = a + delta, s = sign(R_jj)
+// and d_c = W(:,j)^T W(:,c), the update of row j reads
+//   beta = -s (a + delta),  delta = ||W(:,j)||^2 / (a + ||x||),
+//   R_jc  <- -R_jc + (delta R_jc - s d_c) / b,
+//   f_c    = (d_c / (a + b) + s R_jc) / b,
+// so the working arithmetic only forms the corrections delta and (delta R_jc - s d_c) / b,
+// which are of the size of this tile's contribution; the sign flip is exact and the
+// correction is added to the carried value with an error far below FP64's.  The rounding
+// errors of the corrections are relative to one tile's rows, independent from tile to
+// tile, and average out over the tiles instead of accumulating in R (double-float rounding
+// on R itself would grow like the square root of the number of tiles).
 #pragma once
 
 #include "common.cuh"
@@ -58,7 +71,7 @@ struct TsqrSmem {
   static constexpr size_t kStages = kStage * Sh::STAGES;
   static constexpr size_t kMerge = sizeof(double) * 2 * NC * NC;     // [Ra; Rb]
   static constexpr size_t kArena = kStages > kMerge ? kStages : kMerge;
-  static constexpr size_t kR = sizeof(V) * NC * NC;                  // running triangle
+  static constexpr size_t kR = (sizeof(typename Ar::RT) * NC * NC + 15) / 16 * 16;  // running triangle (carried type)
   static constexpr size_t kPart = sizeof(V) * NC * Sh::TR;           // column partial sums
   static constexpr size_t kPiv = (TC > 1) ? sizeof(V) * Sh::B : 0;   // pivot broadcast
   static constexpr size_t kF = sizeof(V) * NC;                       // reflector coefficients
@@ -69,7 +82,8 @@ struct TsqrSmem {
   static constexpr size_t kOffCn = kOffF + kF;                       // running column norms
   static constexpr size_t kOffMisc = kOffCn + sizeof(V) * NC;        // int[16] + int[NC]
   static constexpr size_t kOffSd = (kOffMisc + (16 + NC) * sizeof(int) + 15) / 16 * 16;
-  static constexpr size_t kBytes = kOffSd + 2 * sizeof(double) * NC;  // FP64 scratch
+  static constexpr size_t kOffBeta = kOffSd + 2 * sizeof(double) * NC;  // FP64 scratch, then the new diagonal
+  static constexpr size_t kBytes = kOffBeta + 16;
 };
 
 template <int P>
@@ -101,8 +115,10 @@ struct TsqrCta {
   using V = typename Ar::T;
   static constexpr int TR = Sh::TR, NCT = Sh::NCT, B = Sh::B;
 
+  using RT = typename Ar::RT;
   S* stage;     // [NC][B]
-  V* R;         // [NC][NC], R[j * NC + c] = R(j, c)
+  RT* R;        // [NC][NC], R[j * NC + c] = R(j, c) in the carried type (triple-float or FP64)
+  RT* beta_s;   // the new diagonal of the current column step
   V* part;      // [NC][TR]
   V* piv;       // [B]
   V* fco;       // [NC]
@@ -117,7 +133,8 @@ struct TsqrCta {
   QL_DEV void init(unsigned char* smem) {
     stage = reinterpret_cast<S*>(smem);
     arena = reinterpret_cast<double*>(smem);
-    R = reinterpret_cast<V*>(smem + Sm::kOffR);
+    R = reinterpret_cast<RT*>(smem + Sm::kOffR);
+    beta_s = reinterpret_cast<RT*>(smem + Sm::kOffBeta);
     part = reinterpret_cast<V*>(smem + Sm::kOffPart);
     piv = reinterpret_cast<V*>(smem + Sm::kOffPiv);
     fco = reinterpret_cast<V*>(smem + Sm::kOffF);
@@ -131,7 +148,7 @@ struct TsqrCta {
   }
 
   QL_DEV void reset_r() {
-    for (int i = tid; i < NC * NC; i += T) R[i] = Ar::zero();
+    for (int i = tid; i < NC * NC; i += T) R[i] = Ar::r_zero();
     for (int i = tid; i < NC; i += T) colmax[i] = 0;
   }
 
@@ -249,37 +266,43 @@ struct TsqrCta {
         // Householder preserves the 2-norm of column j of [R; W]: cn[j] + x1^2 + nr is its
         // norm at the start of the tile.  A remainder below kTau of it is rounding residue
         // (a tile with fewer independent rows than columns): no reflector is built from it.
-        V x1 = R[j * NC + j];
+        const RT x1r = R[j * NC + j];
+        const V x1 = Ar::r_get(x1r);
         V rem = Ar::add(Ar::mul(x1, x1), nr);
         bool skip = Ar::is_zero(nr) || Ar::le(rem, Ar::mul(Ar::add(cn[j], rem), Ar::tau2()));
         if (skip) {
           fco[c] = Ar::zero();  // H = I
           if (c == j) misc[0] = 0;
           if (c > j) {
-            V rjc = R[j * NC + c];
+            V rjc = Ar::r_get(R[j * NC + c]);
             cn[c] = Ar::add(cn[c], Ar::mul(rjc, rjc));
           }
         } else {
-          V nrm = Ar::sqrt_(rem);
-          V beta = Ar::negative(x1) ? nrm : Ar::neg(nrm);
-          V v1 = Ar::sub(x1, beta);
+          const bool neg = Ar::r_negative(x1r);  // s = sign(R_jj), sign(0) = +1
+          const V a = neg ? Ar::neg(x1) : x1;
+          const V q = Ar::recip(Ar::add(a, Ar::sqrt_(rem)));  // 1 / (a + ||x||)
+          const V delta = Ar::mul(nr, q);                    // |beta| - a
           if (c == j) {
-            fco[j] = beta;  // the new diagonal, written into R after the barrier
+            const RT b = Ar::r_add(neg ? Ar::r_neg(x1r) : x1r, delta);  // |beta| = a + delta
+            *beta_s = neg ? b : Ar::r_neg(b);  // beta = -s |beta|, written into R after the barrier
             misc[0] = 1;
           } else {
-            V g = Ar::recip(Ar::neg(Ar::mul(beta, v1)));
-            V rjc = R[j * NC + c];
-            V f = Ar::mul(Ar::add(d, Ar::mul(v1, rjc)), g);
-            V rn = Ar::sub_mul(rjc, v1, f);
-            R[j * NC + c] = rn;
+            const V ib = Ar::recip(Ar::add(a, delta));  // 1 / |beta|
+            const RT rjcr = R[j * NC + c];
+            const V rjc = Ar::r_get(rjcr);
+            const V sdc = neg ? Ar::neg(d) : d;      // s d_c
+            const V srjc = neg ? Ar::neg(rjc) : rjc;  // s R_jc
+            const V corr = Ar::mul(Ar::sub(Ar::mul(delta, rjc), sdc), ib);
+            R[j * NC + c] = Ar::r_add(Ar::r_neg(rjcr), corr);  // -R_jc + corr
+            const V rn = Ar::sub(corr, rjc);
             cn[c] = Ar::add(cn[c], Ar::mul(rn, rn));
-            fco[c] = f;
+            fco[c] = Ar::mul(Ar::add(Ar::mul(d, q), srjc), ib);
           }
         }
       }
     }
     __syncthreads();
-    if (tid == 0 && misc[0]) R[j * NC + j] = fco[j];
+    if (tid == 0 && misc[0]) R[j * NC + j] = *beta_s;
     // update my columns c > j
 #pragma unroll
     for (int k = 0; k < NCT; ++k) {
@@ -329,13 +352,15 @@ struct TsqrCta {
   }
 
   // Range verdict of this CTA (double-float policy): every nonzero column max exponent
-  // must lie in [kDfEminLimit, kDfEmaxLimit].
-  QL_DEV bool out_of_range(int n) {
+  // must lie in [kDfEminLimit, df_emax_limit(m)] (the running column norms, formed in the
+  // working arithmetic, reach sqrt(m) max|x|).
+  QL_DEV bool out_of_range(int n, int64_t m) {
     if constexpr (!Ar::kRangeChecked) return false;
+    const int emax = df_emax_limit(m);
     bool bad = false;
     for (int c = 0; c < n; ++c) {
       int e = colmax[c];
-      if (e != 0 && (e < kDfEminLimit || e > kDfEmaxLimit)) bad = true;
+      if (e != 0 && (e < kDfEminLimit || e > emax)) bad = true;
     }
     return bad;
   }

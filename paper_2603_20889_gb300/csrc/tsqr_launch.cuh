@@ -46,12 +46,12 @@ __global__ void __launch_bounds__(T, 1) tsqr_kernel(TsqrArgs<S> a) {
   cta.run(a.p, 0, t0, t1);
 
   const int n = a.p.n;
-  if (threadIdx.x == 0 && cta.out_of_range(n)) atomicOr(&a.tv.flags[0], 1);
+  if (threadIdx.x == 0 && cta.out_of_range(n, a.p.m)) atomicOr(&a.tv.flags[0], 1);
   // leaf triangle -> slot(0, bid), FP64 (hi + lo of a double-float is exact in a double)
   double* slot = a.tv.slots + (size_t)bid * n * n;
   for (int i = threadIdx.x; i < n * n; i += T) {
     int c = i / n, r = i % n;
-    __stcg(slot + i, r <= c ? Ar::to_double(cta.R[r * NC + c]) : 0.0);
+    __stcg(slot + i, r <= c ? Ar::r_to_double(cta.R[r * NC + c]) : 0.0);
   }
   double* Ra = cta.arena;
   double* Rb = cta.arena + NC * NC;

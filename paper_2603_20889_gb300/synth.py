@@ -94,6 +94,44 @@ def lstsq_case(m: int, n: int, kappa: float, seed: int, noise: float = 1e-6, dty
     return np.asfortranarray(A.astype(dtype)), b.astype(dtype), x_star
 
 
+def conditioned_upper(n: int, kappa: float, seed: int, bits: int = 40) -> np.ndarray:
+    """An upper triangular R0 = T1 diag(sigma) T2 with positive diagonal, rounded to
+    multiples of 2^-bits: T1, T2 unit upper triangular with off-diagonal entries uniform in
+    [-1/(2n), 1/(2n)] (row sums below 1/2, so kappa(T) <= 3) and sigma the geometric
+    spectrum from 1 to 1/kappa; kappa(R0) lies within a factor 9 of kappa.  Column j of R0
+    carries the larger scales sigma_i (i < j) above its diagonal, so the columns of
+    H R0 are nearly dependent in the way that makes Householder cancel."""
+    rng = np.random.default_rng(seed + 7717)
+    c = 0.5 / max(n, 1)
+    T1 = np.eye(n) + np.triu(rng.uniform(-c, c, (n, n)), 1)
+    T2 = np.eye(n) + np.triu(rng.uniform(-c, c, (n, n)), 1)
+    R0 = np.triu((T1 * spectrum(n, kappa)) @ T2)
+    return np.ldexp(np.rint(np.ldexp(R0, bits)), -bits)
+
+
+def walsh_indices(m: int, n: int, seed: int) -> np.ndarray:
+    """n distinct column indices of the m x m Sylvester Hadamard matrix, drawn at random."""
+    rng = np.random.default_rng(seed + 3571)
+    return np.sort(rng.choice(m, size=n, replace=False)).astype(np.int64)
+
+
+def hadamard_exact_case(m: int, n: int, kappa: float, seed: int):
+    """(X, R_exact) with X = H[:, J] R0: J random distinct Hadamard columns (orthogonal, norm
+    sqrt(m), rows that look random), R0 = conditioned_upper(n, kappa).  The entries of X are
+    sums of at most n multiples of 2^-40 below 1.5 in size, exact in FP64, and X^T X =
+    m R0^T R0 exactly, so R = sqrt(m) R0 (m a power of two)."""
+    if m & (m - 1) or m < n:
+        raise ValueError("m must be a power of two and >= n")
+    R0 = conditioned_upper(n, kappa, seed)
+    J = walsh_indices(m, n, seed)
+    i = np.arange(m, dtype=np.int64)
+    X = np.zeros((m, n), order="F")
+    for k in range(n):
+        h = 1.0 - 2.0 * (np.bitwise_count(i & J[k]) & 1)
+        X[:, k:] += h[:, None] * R0[k, k:][None, :]
+    return X, math.sqrt(m) * R0
+
+
 # --------------------------------------------------------------------------- device
 
 
@@ -136,6 +174,26 @@ def hadamard_device(m: int, n: int, seed: int, device="cuda", dtype=None):
         # X[:, c] += H[:, j] * R0[j, c]  (R0 is upper triangular)
         Xt += torch.from_numpy(R0[j, :]).to(device).unsqueeze(1) * h.unsqueeze(0)
     return Xt.to(dtype), math.sqrt(m) * R0
+
+
+def hadamard_exact_device(m: int, n: int, kappa: float, seed: int, device="cuda"):
+    """Device-resident `hadamard_exact_case`: ((n, m) FP64 tensor, R_exact numpy).  The sums
+    are exact in any order, so the device X equals the host one bit for bit."""
+    import torch
+
+    R0 = conditioned_upper(n, kappa, seed)
+    J = walsh_indices(m, n, seed)
+    i = torch.arange(m, device=device, dtype=torch.int64)
+    Xt = torch.zeros((n, m), dtype=torch.float64, device=device)
+    R0d = torch.from_numpy(R0).to(device)
+    for k in range(n):
+        b = i & int(J[k])
+        for sh in (32, 16, 8, 4, 2, 1):  # parity of popcount(i & J_k)
+            b = b ^ (b >> sh)
+        h = 1.0 - 2.0 * (b & 1).to(torch.float64)
+        Xt[k:, :] += R0d[k, k:].unsqueeze(1) * h.unsqueeze(0)
+        del b, h
+    return Xt, math.sqrt(m) * R0
 
 
 # --------------------------------------------------------------------------- batched / serving

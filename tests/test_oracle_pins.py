@@ -66,6 +66,31 @@ def test_hadamard_construction_is_exact(m, n):
     assert np.max(np.abs(R - R_exact)) <= 64 * EPS * np.max(np.abs(R_exact))
 
 
+@pytest.mark.parametrize("m,n,kappa", [(1 << 12, 8, 1e4), (1 << 13, 16, 1e6), (1 << 12, 1, 1.0), (1 << 11, 33, 1e2)])
+def test_random_walsh_columns_give_the_exact_r(m, n, kappa):
+    """X = H[:, J] R0 with J random Hadamard columns and R0 a short-mantissa triangle: X is
+    exact in FP64 and R = sqrt(m) R0 (the full-size accuracy reference of the benchmark)."""
+    X, R_exact = synth.hadamard_exact_case(m, n, kappa, seed=n + 11)
+    # H[:, J] has orthogonal columns of norm sqrt(m): the exact Gram is m R0^T R0
+    R0 = R_exact / np.sqrt(m)
+    assert np.allclose(X.T @ X, m * (R0.T @ R0), rtol=0, atol=64 * EPS * m * np.max(np.abs(R0)) ** 2 * n)
+    R = oracle.householder_r(X)
+    k = oracle.kappa2(R_exact)
+    assert k < 10 * max(kappa, 1.0)
+    assert oracle.rel_err(R, R_exact) <= 1e-15 * n * k
+    assert oracle.row_err(R, R_exact) <= 1e-15 * n * k
+
+
+def test_row_err_sees_a_wrong_last_row():
+    """The row-scaled measure catches what the Frobenius ratio cannot at large kappa."""
+    n, kappa = 16, 1e6
+    R0 = synth.conditioned_upper(n, kappa, seed=5)
+    bad = R0.copy()
+    bad[-1, -1] *= 2.0  # the smallest row entirely wrong
+    assert oracle.rel_err(bad, R0) <= oracle.tolerance(n, kappa)
+    assert oracle.row_err(bad, R0) > oracle.tolerance(n, kappa)
+
+
 # ---------------------------------------------------------------- exact arithmetic
 
 
