@@ -124,8 +124,7 @@ QL_DEV bool mbar_wait_bounded(uint64_t* mbar, uint32_t parity, long long limit =
   return true;
 }
 QL_DEV void mbar_arrive(uint64_t* mbar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];
-" ::"r"(smem_addr(mbar)) : "memory");
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_addr(mbar)) : "memory");
 }
 QL_DEV void mbar_arrive_expect_tx(uint64_t* mbar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(mbar)), "r"(bytes)
