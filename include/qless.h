@@ -238,6 +238,10 @@ typedef struct {
   double* R;             /* n x n (kind 0) or (n+1) x (n+1) (kind 1), ld = rows */
   double* x;             /* kind 1: solution (n entries) and x[n] = residual norm */
   int32_t* info;         /* nullable int32[2] */
+  int32_t method_hint;   /* QL_AUTO (0 in a zeroed struct is QL_TSQR; set QL_AUTO to let the
+                            tuner choose), QL_TSQR or QL_CHOLQR2 */
+  double kappa_hint;     /* estimate of kappa_2(X); <= 0: unknown (the Gram method is only
+                            chosen automatically for a known kappa_hint <= 1e6) */
 } ql_problem;
 
 /*
@@ -286,6 +290,7 @@ typedef struct {
   int32_t kind;       /* 0: R only; 1: least squares on [X b] */
   const void* b;      /* kind 1 */
   double kappa_hint;  /* <= 0: unknown */
+  int32_t method_hint; /* as ql_problem::method_hint */
 } ql_request;
 
 typedef struct {
@@ -319,6 +324,10 @@ ql_status ql_server_submit(ql_server* s, const ql_request* req, uint64_t* ticket
 ql_status ql_server_poll(ql_server* s, uint64_t ticket, ql_result* out);
 /* Frees the result's device buffers (returns them to the budget). */
 ql_status ql_server_release(ql_server* s, uint64_t ticket);
+/* Withdraws a request that is still queued (not yet admitted to a group): QL_OK, and the
+ * ticket becomes unknown; QL_ERR_BUSY once it has been launched (it then completes and is
+ * polled and released as usual); QL_ERR_UNKNOWN for an unknown ticket. */
+ql_status ql_server_cancel(ql_server* s, uint64_t ticket);
 ql_status ql_server_drain(ql_server* s, double timeout_s);
 ql_status ql_server_stats(ql_server* s, ql_stats* out);
 void ql_server_destroy(ql_server* s);

@@ -63,6 +63,7 @@ SIGNATURES = {
     "ql_server_submit": (_i32, [_vp, _vp, _vp]),
     "ql_server_poll": (_i32, [_vp, ctypes.c_uint64, _vp]),
     "ql_server_release": (_i32, [_vp, ctypes.c_uint64]),
+    "ql_server_cancel": (_i32, [_vp, ctypes.c_uint64]),
     "ql_server_drain": (_i32, [_vp, _f64]),
     "ql_server_stats": (_i32, [_vp, _vp]),
     "ql_server_destroy": (None, [_vp]),
@@ -73,14 +74,15 @@ class Problem(ctypes.Structure):
     """ql_problem: one problem of a batch (device pointers)."""
     _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("ld", ctypes.c_int64), ("X", ctypes.c_void_p),
                 ("dtype", ctypes.c_int32), ("kind", ctypes.c_int32), ("b", ctypes.c_void_p),
-                ("R", ctypes.c_void_p), ("x", ctypes.c_void_p), ("info", ctypes.c_void_p)]
+                ("R", ctypes.c_void_p), ("x", ctypes.c_void_p), ("info", ctypes.c_void_p),
+                ("method_hint", ctypes.c_int32), ("kappa_hint", ctypes.c_double)]
 
 
 class Request(ctypes.Structure):
     """ql_request: one serving request (device pointers)."""
     _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("ld", ctypes.c_int64), ("X", ctypes.c_void_p),
                 ("dtype", ctypes.c_int32), ("kind", ctypes.c_int32), ("b", ctypes.c_void_p),
-                ("kappa_hint", ctypes.c_double)]
+                ("kappa_hint", ctypes.c_double), ("method_hint", ctypes.c_int32)]
 
 
 class Result(ctypes.Structure):

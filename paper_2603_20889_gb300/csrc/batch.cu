@@ -87,6 +87,7 @@ QL_DEV void batch_chunk(const BatchItem& it, int64_t chunk, unsigned char* smem,
   p.src.nA = it.nA;
   p.m = it.m;
   p.n = it.n;
+  p.vec16 = 0;
   const int64_t t0 = chunk * it.tiles_per_chunk;
   const int64_t t1 = min(it.tiles, t0 + it.tiles_per_chunk);
   cta.run(p, 0, t0, t1);
@@ -106,8 +107,7 @@ QL_DEV void batch_chunk(const BatchItem& it, int64_t chunk, unsigned char* smem,
     __stcg(slot + i, r <= c ? Ar::r_to_double(cta.R[r * NC + c]) : 0.0);
   }
   double* Ra = cta.arena;
-  double* Rb = cta.arena + NC * NC;
-  if (!climb_tree<NC, T>(tv, (int)chunk, n, Ra, Rb, cta.sd, &cta.misc[1])) return;
+  if (!climb_tree<NC, T, tree_arity<NC>()>(tv, (int)chunk, n, cta.arena, cta.sd, &cta.misc[1])) return;
   __threadfence();
   if (Ar::kRangeChecked && *(volatile int*)&flags[it.flag_idx] != 0) return;
   if (it.kind == 0)

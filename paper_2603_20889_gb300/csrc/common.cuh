@@ -46,10 +46,12 @@ QL_DEV df df_add(df a, df b) {  // "sloppy" sum: absolute error ~ u^2 (|a| + |b|
 }
 QL_DEV df df_neg(df a) { return df{-a.hi, -a.lo}; }
 QL_DEV df df_sub(df a, df b) { return df_add(a, df_neg(b)); }
+// Products keep the lo * lo term: it is below 2^-48 of the product but has a fixed sign for
+// squares (a dropped lo^2 biases every sum of squares low by about 2^-50).
 QL_DEV df df_mul(df a, df b) {
   float p = __fmul_rn(a.hi, b.hi);
   float e = __fmaf_rn(a.hi, b.hi, -p);
-  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.lo, e));
   e = __fmaf_rn(a.lo, b.hi, e);
   return df_make(p, e);
 }
@@ -57,28 +59,35 @@ QL_DEV df df_mul(df a, df b) {
 QL_DEV df df_sub_mul(df a, df b, df c) {
   float p = __fmul_rn(b.hi, c.hi);
   float e = __fmaf_rn(b.hi, c.hi, -p);
-  e = __fmaf_rn(b.hi, c.lo, e);
+  e = __fmaf_rn(b.hi, c.lo, __fmaf_rn(b.lo, c.lo, e));
   e = __fmaf_rn(b.lo, c.hi, e);
   float s, t;
   two_sum(a.hi, -p, s, t);
   t = __fadd_rn(t, __fsub_rn(a.lo, e));
   return df_make(s, t);
 }
-QL_DEV df df_recip(df b) {  // 1 / b: one Newton correction of the float reciprocal
+// 1 / b from the float reciprocal q and r = 1 - q b: 1 / b = q (1 + r + r^2 + ...).  The
+// second-order term q r^2 is kept: one Newton step alone always falls short (by q r^2 >= 0,
+// about 2^-50 on average), a one-signed error that would accumulate over many updates.
+QL_DEV df df_recip(df b) {
   float q = __fdiv_rn(1.0f, b.hi);
   float p = __fmul_rn(q, b.hi);
   float e = __fmaf_rn(q, b.hi, -p);
   e = __fmaf_rn(q, b.lo, e);
   float r = __fsub_rn(__fsub_rn(1.0f, p), e);  // 1 - q b
-  return df_make(q, __fmul_rn(r, q));
+  return df_make(q, __fmul_rn(__fmaf_rn(r, r, r), q));
 }
-QL_DEV df df_sqrt(df a) {  // sqrt(a), a >= 0: one Newton correction of sqrtf
+// sqrt(a), a >= 0: sqrtf plus the series correction d - d^2 / (2 s), d = r / (2 s),
+// r = a - s^2 (one Newton step alone always overshoots by about d^2 / (2 s)).
+QL_DEV df df_sqrt(df a) {
   if (a.hi <= 0.0f) return df{0.0f, 0.0f};
   float s = __fsqrt_rn(a.hi);
   float p = __fmul_rn(s, s);
   float e = __fmaf_rn(s, s, -p);
   float r = __fadd_rn(__fsub_rn(__fsub_rn(a.hi, p), e), a.lo);
-  return df_make(s, __fdiv_rn(r, __fmul_rn(2.0f, s)));
+  float is2 = __fdiv_rn(0.5f, s);
+  float d = __fmul_rn(r, is2);
+  return df_make(s, __fmaf_rn(-__fmul_rn(d, d), is2, d));
 }
 QL_DEV double df_to_double(df a) { return (double)a.hi + (double)a.lo; }
 QL_DEV df df_from_double_rn(double x) {  // used only on n x n data
@@ -153,10 +162,10 @@ struct ArithDF {
     return e == 0 ? df{0.0f, 0.0f} : df{x, 0.0f};
   }
   QL_DEV static Acc acc_zero() { return Acc{0.0f, 0.0f}; }
-  QL_DEV static void acc_fma(Acc& acc, T a, T b) {  // acc += a * b
+  QL_DEV static void acc_fma(Acc& acc, T a, T b) {  // acc += a * b (lo * lo kept, see df_mul)
     float p = __fmul_rn(a.hi, b.hi);
     float e = __fmaf_rn(a.hi, b.hi, -p);
-    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.lo, e));
     e = __fmaf_rn(a.lo, b.hi, e);
     float s, t;
     two_sum(acc.hi, p, s, t);
@@ -264,6 +273,11 @@ QL_DEV void cp_async_8(void* smem, const void* gmem, bool valid) {
 QL_DEV void cp_async_4(void* smem, const void* gmem, bool valid) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(smem_addr(smem)), "l"(gmem),
                "r"(valid ? 4 : 0));
+}
+// 16-byte copy (both addresses 16-byte aligned) of which the first src_bytes (0..16) are
+// read and the rest zero-filled.
+QL_DEV void cp_async_16(void* smem, const void* gmem, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_addr(smem)), "l"(gmem), "r"(src_bytes));
 }
 QL_DEV void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 QL_DEV void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }

@@ -49,7 +49,54 @@ struct GramArgs {
   double* Rext;
   int32_t* info;
   int bulk;  // every column starts 16-byte aligned: full tiles load with bulk copies
+  // How the next pass's kernel reads the carried M (so that the epilogue can carry the exact
+  // inverse of what it applies): 0 FP64 as is, 1 double-float per entry, 2 the tensor-core
+  // slicing (48-bit fixed point per column of M' = diag(2^e_k) M).
+  int mround;
 };
+
+// Round the upper triangular M (n x n, row-major ld LE in shared memory) the way the next
+// pass's kernel reads it (GramArgs::mround), in place.  colexp[k] is the largest biased
+// exponent of column k of X (the tensor-core kernels scale row k of M by 2^(colexp[k] - 1022)).
+template <int T>
+QL_DEV void round_m_like_consumer(double* Ms, int ldm, int n, int mround, const int* colexp) {
+  if (mround == 1) {
+    for (int e = threadIdx.x; e < n * n; e += T) {
+      double& v = Ms[(e / n) * ldm + e % n];
+      const float hi = __double2float_rn(v);
+      const float lo = __double2float_rn(v - (double)hi);
+      v = (double)hi + (double)lo;
+    }
+  } else if (mround == 2) {
+    for (int j = threadIdx.x; j < n; j += T) {  // one column per thread
+      for (int it = 0; it < 4; ++it) {           // a value that rounds up to the next binade moves F
+        int F = 0;
+        for (int k = 0; k <= j; ++k) {
+          const int ek = colexp[k];
+          const double v = ek > 0 ? Ms[k * ldm + j] * __longlong_as_double((long long)(ek + 1) << 52) : 0.0;
+          F = max(F, (int)((__double_as_longlong(v) >> 52) & 0x7ff));
+        }
+        if (F == 0) break;
+        bool moved = false;
+        for (int k = 0; k <= j; ++k) {
+          const int ek = colexp[k];
+          if (ek <= 0) {
+            Ms[k * ldm + j] = 0.0;
+            continue;
+          }
+          const double sc = __longlong_as_double((long long)(ek + 1) << 52);  // 2^(ek - 1022)
+          const double v = Ms[k * ldm + j] * sc;
+          // the value the kernel's digits represent: N 2^(F - 1022 - 48)
+          const double r = (double)fixed48_of_double(v, F) * __longlong_as_double((long long)(F - 48 + 1) << 52);
+          if (((__double_as_longlong(r) >> 52) & 0x7ff) > F) moved = true;
+          Ms[k * ldm + j] = r / sc;
+        }
+        if (!moved) break;
+      }
+    }
+  }
+  __syncthreads();
+}
 
 QL_DEV double qnan() { return __longlong_as_double(0x7ff8000000000000ll); }
 
@@ -313,6 +360,13 @@ QL_DEV void gram_finish(const GramArgs<S>& a, unsigned char* smem, const int* co
         __syncthreads();
       }
       tri_upper_inverse<T>(Cs, LE, Us, LE, n);
+      if (a.mround) {
+        // the next pass applies M rounded as its kernel reads it; carry that M and, as R,
+        // its exact inverse, so that R_last ... R1 stays consistent with the Y it formed
+        __syncthreads();
+        round_m_like_consumer<T>(Us, LE, n, a.mround, a.w.flags + 64);
+        tri_upper_inverse<T>(Us, LE, Cs, LE, n);
+      }
       for (int e = tid; e < nn; e += T) {
         keep[e] = Cs[(e / n) * LE + e % n];
         keep[nn + e] = Us[(e / n) * LE + e % n];
@@ -366,6 +420,229 @@ QL_DEV void gram_finish(const GramArgs<S>& a, unsigned char* smem, const int* co
     epilogue_lstsq<T>(Ps, LE, n, a.x, a.resnorm, a.Rext, a.info, vec, sflag, tmo);
 }
 
+
+// ---------------------------------------------------------------------------------------
+// Streaming Gram pass for narrow X (n <= 4).  There is no shared-memory staging: every
+// thread loads 16-byte vectors of its columns straight into registers (U of them per column
+// in flight), converts them, applies M in the later passes (M in shared memory, read by
+// broadcast) and adds the n (n + 1) / 2 products of each row into its own accumulators.
+// A thread sums only m / (CTAs x 256) rows, so its double-float sums stay short; they are
+// added across the warp by shuffles and across warps and CTAs in FP64, then the same
+// last-CTA epilogue as the other Gram kernels runs.
+// ---------------------------------------------------------------------------------------
+template <int NC>
+struct StreamShape {
+  static constexpr int T = 256;
+  static constexpr int U = NC <= 2 ? 4 : (NC <= 4 ? 2 : 1);  // 16-byte loads in flight per column
+  static constexpr int NE = NC * (NC + 1) / 2;                 // upper-triangle entries
+};
+
+template <int NC, typename S, typename Ar>
+struct StreamSmem {
+  using Sh = StreamShape<NC>;
+  static constexpr size_t kM = sizeof(typename Ar::T) * NC * NC;
+  static constexpr size_t kOffRed = (kM + 15) / 16 * 16;
+  static constexpr size_t kOffMisc = kOffRed + sizeof(double) * (Sh::T / 32) * Sh::NE;
+  static constexpr size_t kMain = kOffMisc + (64 + NC) * sizeof(int);
+  static constexpr size_t kEpi = GramSmem<NC, S, Ar>::kEpi + 64 * sizeof(int) + 16;
+  static constexpr size_t kBytes = kMain > kEpi ? kMain : kEpi;
+};
+
+template <typename S>
+QL_DEV void load16(S (&v)[16 / sizeof(S)], const S* p);
+template <>
+QL_DEV void load16<double>(double (&v)[2], const double* p) {
+  const double2 t = __ldg(reinterpret_cast<const double2*>(p));
+  v[0] = t.x;
+  v[1] = t.y;
+}
+template <>
+QL_DEV void load16<float>(float (&v)[4], const float* p) {
+  const float4 t = __ldg(reinterpret_cast<const float4*>(p));
+  v[0] = t.x;
+  v[1] = t.y;
+  v[2] = t.z;
+  v[3] = t.w;
+}
+
+template <int NC, typename S, typename Ar, int XF>
+__global__ void __launch_bounds__(StreamShape<NC>::T) gram_stream_kernel(GramArgs<S> a) {
+  using Sh = StreamShape<NC>;
+  using Sm = StreamSmem<NC, S, Ar>;
+  using V = typename Ar::T;
+  using Acc = typename Ar::Acc;
+  constexpr int T = Sh::T, U = Sh::U, NE = Sh::NE, EPV = 16 / (int)sizeof(S), NW = T / 32;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, n = a.n;
+
+  if (a.gated && *(volatile int*)&a.w.flags[0] == 0) return;
+  if (Ar::kRangeChecked && a.pass >= 2 && *(volatile int*)&a.w.flags[0] != 0) return;  // FP64 redoes it
+  if (a.pass >= 2 && *(volatile int*)&a.w.flags[1] != 0) {  // first pass broke down
+    if (blockIdx.x == 0) write_nan_outputs(a, T);
+    return;
+  }
+  V* Mv = reinterpret_cast<V*>(smem);
+  double* red = reinterpret_cast<double*>(smem + Sm::kOffRed);
+  int* misc = reinterpret_cast<int*>(smem + Sm::kOffMisc);
+  int* colmax = misc + 64;
+  for (int i = tid; i < NC; i += T) colmax[i] = 0;
+  if constexpr (XF != kXNone) {
+    const double* M = a.w.keep + (size_t)n * n;  // the previous pass's M (row-major, ld n)
+    for (int i = tid; i < NC * NC; i += T) {
+      const int r = i / NC, c = i % NC;
+      Mv[i] = (r < n && c < n) ? Ar::from_double(__ldcg(M + r * n + c)) : Ar::zero();
+    }
+  }
+  __syncthreads();
+
+  Acc acc[NE];
+#pragma unroll
+  for (int e = 0; e < NE; ++e) acc[e] = Ar::acc_zero();
+  unsigned emax[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) emax[c] = 0;
+  const S* col[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) col[c] = a.src.col(c < n ? c : 0);
+
+  // this CTA's rows, in 16-byte units of EPV rows
+  const int64_t units = (a.m + EPV - 1) / EPV;
+  const int64_t u0 = units * blockIdx.x / gridDim.x, u1 = units * (blockIdx.x + 1) / gridDim.x;
+  for (int64_t ub = u0; ub < u1; ub += (int64_t)T * U) {
+    S vals[U][NC][EPV];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t uu = ub + (int64_t)u * T + tid;
+      const int64_t row = uu * EPV;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        if (c < n && uu < u1 && a.bulk && row + EPV <= a.m) {
+          load16<S>(vals[u][c], col[c] + row);
+        } else {
+#pragma unroll
+          for (int e = 0; e < EPV; ++e)
+            vals[u][c][e] = (c < n && uu < u1 && row + e < a.m) ? __ldg(col[c] + row + e) : S(0);
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int e = 0; e < EPV; ++e) {
+        V y[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          int E;
+          y[c] = Ar::load(vals[u][c][e], E);
+          if constexpr (Ar::kRangeChecked) emax[c] = max(emax[c], (unsigned)E);
+        }
+        if constexpr (XF != kXNone) {  // y = x M, one row
+          V x[NC];
+#pragma unroll
+          for (int c = 0; c < NC; ++c) x[c] = y[c];
+#pragma unroll
+          for (int j = 0; j < NC; ++j) {
+            Acc s = Ar::acc_zero();
+#pragma unroll
+            for (int k = 0; k < NC; ++k)
+              if (XF != kXUpper || k <= j) Ar::acc_fma(s, x[k], Mv[k * NC + j]);
+            y[j] = Ar::acc_get(s);
+          }
+        }
+        int ei = 0;
+#pragma unroll
+        for (int i = 0; i < NC; ++i)
+#pragma unroll
+          for (int j = i; j < NC; ++j) Ar::acc_fma(acc[ei++], y[i], y[j]);
+      }
+  }
+
+  if constexpr (Ar::kRangeChecked) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const unsigned em = __reduce_max_sync(0xffffffffu, emax[c]);
+      if (lane == 0 && em > 0) atomicMax(&colmax[c], (int)em);
+    }
+  }
+  // warp sums (shuffles), then warps and CTAs in FP64
+#pragma unroll
+  for (int e = 0; e < NE; ++e) {
+    V v = Ar::acc_get(acc[e]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = Ar::add(v, Ar::shfl(v, o));
+    if (lane == 0) red[warp * NE + e] = Ar::to_double(v);
+  }
+  __syncthreads();
+  double* part = a.w.partials + (size_t)blockIdx.x * NC * NC;
+  for (int e = tid; e < NE; e += T) {
+    double v = 0.0;
+    for (int w = 0; w < NW; ++w) v += red[w * NE + e];
+    int i = 0, rem = e;
+    while (rem >= NC - i) {
+      rem -= NC - i;
+      ++i;
+    }
+    __stcg(part + i * NC + (i + rem), v);
+  }
+  gram_finish<NC, T, S, Ar>(a, smem, colmax, misc);
+}
+
+template <int NC, typename S, typename Ar, int XF>
+ql_status gram_stream_launch_one(const GramCall& c, const GramWs& w, int pass, int gated) {
+  using Sh = StreamShape<NC>;
+  using Sm = StreamSmem<NC, S, Ar>;
+  auto kern = gram_stream_kernel<NC, S, Ar, XF>;
+  static int occ = 0;
+  static std::mutex mu;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (occ == 0) {
+      if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sm::kBytes) != cudaSuccess)
+        return QL_ERR_CUDA;
+      int o = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, Sh::T, Sm::kBytes) != cudaSuccess)
+        return QL_ERR_CUDA;
+      occ = o < 1 ? 1 : (o > kGramMaxCtasPerSm ? kGramMaxCtasPerSm : o);
+    }
+  }
+  constexpr int EPV = 16 / (int)sizeof(S);
+  const int64_t units = (c.m + EPV - 1) / EPV;
+  int64_t g = (int64_t)device_sm_count() * occ;
+  const int64_t need = (units + (int64_t)Sh::T * Sh::U - 1) / ((int64_t)Sh::T * Sh::U);  // one sweep per CTA at least
+  if (g > need) g = need;
+  if (g < 1) g = 1;
+  GramArgs<S> a{};
+  a.src.A = static_cast<const S*>(c.A);
+  a.src.lda = c.lda;
+  a.src.b = static_cast<const S*>(c.b);
+  a.src.nA = c.nA;
+  a.m = c.m;
+  a.n = c.n;
+  a.tiles = 0;
+  a.pass = pass;
+  a.method = c.method;
+  a.gated = gated;
+  a.epilogue = c.epilogue;
+  a.w = w;
+  a.R = c.R;
+  a.ldr = c.ldr;
+  a.Z = c.Z;
+  a.rank_tol = c.rank_tol;
+  a.x = c.x;
+  a.resnorm = c.resnorm;
+  a.Rext = c.Rext;
+  a.info = c.info;
+  {
+    auto aligned = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+    bool b = aligned(c.A) && ((size_t)c.lda * sizeof(S)) % 16 == 0;
+    if (c.nA < c.n) b = b && aligned(c.b);
+    a.bulk = b ? 1 : 0;  // 16-byte loads
+  }
+  a.mround = std::is_same<Ar, ArithDF>::value ? 1 : 0;
+  count_launch();
+  kern<<<(int)g, Sh::T, Sm::kBytes, c.stream>>>(a);
+  return cudaPeekAtLastError() == cudaSuccess ? QL_OK : QL_ERR_CUDA;
+}
 
 // Tensor-core Gram pass (double-float policy only): see gram_tc.cuh.
 template <int NC, typename S, int XF>
@@ -779,6 +1056,7 @@ ql_status gram_tc_launch_one(const GramCall& c, const GramWs& w, int pass) {
   a.resnorm = c.resnorm;
   a.Rext = c.Rext;
   a.info = c.info;
+  a.mround = 2;
   count_launch();
   kern<<<(int)g, Sh::T, Sm::kBytes, c.stream>>>(a);
   return cudaPeekAtLastError() == cudaSuccess ? QL_OK : QL_ERR_CUDA;
@@ -1248,6 +1526,7 @@ ql_status gram_umma_launch_one(const GramCall& c, const GramWs& w, int pass) {
     if (c.nA < c.n) b = b && aligned(c.b);
     a.bulk = b ? 1 : 0;
   }
+  a.mround = 2;
   count_launch();
   kern<<<(int)g, umma_threads<XF>(), Sm::kBytes, c.stream>>>(a);
   return cudaPeekAtLastError() == cudaSuccess ? QL_OK : QL_ERR_CUDA;
@@ -1296,6 +1575,7 @@ ql_status gram_launch_one(const GramCall& c, const GramWs& w, int pass, int gate
   a.resnorm = c.resnorm;
   a.Rext = c.Rext;
   a.info = c.info;
+  a.mround = std::is_same<Ar, ArithDF>::value ? 1 : 0;
   count_launch();
   kern<<<(int)g, Sh::T, Sm::kBytes, c.stream>>>(a);
   return cudaPeekAtLastError() == cudaSuccess ? QL_OK : QL_ERR_CUDA;
@@ -1326,6 +1606,14 @@ ql_status gram_dispatch(const GramCall& c, const GramWs& w, int gated) {
           return gram_tc_launch_one<NC, S, kXUpper>(c, w, 3);
         }
       }
+    }
+    if constexpr (NC <= 4) {  // narrow X: the streaming kernel (n = 8 would spill its 36 accumulators)
+      ql_status st = gram_stream_launch_one<NC, S, Ar, kXNone>(c, w, 1, gated);
+      if (st) return st;
+      if (c.method == QL_SVQB2) return gram_stream_launch_one<NC, S, Ar, kXFull>(c, w, 2, gated);
+      st = gram_stream_launch_one<NC, S, Ar, kXUpper>(c, w, 2, gated);
+      if (st || c.method != QL_SCHOLQR3) return st;
+      return gram_stream_launch_one<NC, S, Ar, kXUpper>(c, w, 3, gated);
     }
     ql_status st = gram_launch_one<NC, S, Ar, kXNone>(c, w, 1, gated);
     if (st) return st;

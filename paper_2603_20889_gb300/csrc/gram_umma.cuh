@@ -1,9 +1,9 @@
 // Blackwell 5th-generation tensor-core (tcgen05) primitives and the tile layout of the
 // Gram products C = Y^T Y of the Gram methods (paper Sec. 3.1).
 //
-// The exact bf16 digit slicing of gram_tc.cuh is kept (seven signed base-128 digits per
-// value, digit-pair products with p + q <= 8 summed exactly in FP32), but the products run
-// as tcgen05.mma with the accumulators in tensor memory (TMEM):
+// The exact bf16 digit slicing of gram_tc.cuh is kept (seven balanced base-128 digits per
+// value, digit-pair products with p + q <= 6 (0-based) summed exactly in FP32), but the
+// products run as tcgen05.mma with the accumulators in tensor memory (TMEM):
 //  * Digit planes are stored in shared memory in the canonical K-major layout without
 //    swizzle: 8 x 8 core matrices of 128 contiguous bytes (8 columns c x 8 rows r), core
 //    matrices along r 128 B apart (LBO), 8-column groups KT x 16 B apart (SBO).  A plane
@@ -16,10 +16,11 @@
 //  * Seven blocks (t = 0..6) cover every pair with p + q <= 6 (0-based); lane groups whose
 //    weight exceeds 6 hold products beyond the truncation and are not read.  The plane
 //    after the last one (p = 7) is never needed, so whatever lies there is harmless.
-//  * Per block and tile at most ceil(7 / SP) pairs x KT rows x 127^2 < 2^24 add up: every FP32
+//  * Per block and tile at most ceil(7 / SP) pairs x KT rows x 64^2 < 2^24 add up: every FP32
 //    accumulator is an exact integer.  One thread issues the MMAs and commits them to an
 //    mbarrier; all warps then read TMEM (each warp its lane quarter) and fold the blocks,
-//    scaled by 2^(e_i + e_j - 7(w + 2)), into double-float accumulators.
+//    scaled by 2^(e_i + e_j - 12 - 7w), into double-float accumulators that move into FP64
+//    (in an L2-resident workspace block) every few tiles.
 #pragma once
 
 #include <cstdint>
@@ -40,7 +41,7 @@ struct UmmaShape {
   static constexpr int TCOLS = 7 * NC <= 128 ? 128 : (7 * NC <= 256 ? 256 : 512);  // TMEM columns
   static_assert(NC == 16 || NC == 32 || NC == 64, "M = 128 needs 128 / NC stacked planes");
   static constexpr int PAIRS_MAX = (ND + SP - 1) / SP;  // MMA pairs per accumulator block
-  static_assert(PAIRS_MAX * KT * 127 * 127 < (1 << 24), "exact FP32 digit sums");
+  static_assert(PAIRS_MAX * KT * 64 * 64 < (1 << 24), "exact FP32 digit sums");
 };
 
 template <int NC, typename S>

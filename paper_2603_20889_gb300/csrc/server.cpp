@@ -129,7 +129,7 @@ struct ql_server {
   std::deque<uint64_t> queue;
   std::unordered_map<uint64_t, ql::Req> reqs;
   std::vector<ql::Group> inflight;
-  int64_t submitted = 0, completed = 0, rejected = 0, inflight_reqs = 0;
+  int64_t submitted = 0, completed = 0, rejected = 0, cancelled = 0, inflight_reqs = 0;
   std::vector<double> latencies;
   double t_first = 0, t_last = 0;
 };
@@ -217,6 +217,8 @@ static bool admit_and_launch(ql_server* s) {
     p.R = base;
     p.x = base + n1 * n1;
     p.info = nullptr;  // set below: one status array per group
+    p.method_hint = q.r.method_hint;
+    p.kappa_hint = q.r.kappa_hint;
   }
   // The group's workspace (R-trees) must fit next to its data and outputs: drop requests
   // from the tail (back to the front of the queue, in order) until it does.
@@ -367,6 +369,20 @@ ql_status ql_server_release(ql_server* s, uint64_t ticket) {
   if (it->second.state != 2) return QL_ERR_BUSY;
   s->dev.release(it->second.out_off, it->second.out_bytes);
   s->reqs.erase(it);
+  s->cv.notify_one();
+  return QL_OK;
+}
+
+ql_status ql_server_cancel(ql_server* s, uint64_t ticket) {
+  if (!s) return QL_ERR_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(ticket);
+  if (it == s->reqs.end()) return QL_ERR_UNKNOWN;
+  if (it->second.state != 0) return QL_ERR_BUSY;  // launched (or done): it completes normally
+  auto qi = std::find(s->queue.begin(), s->queue.end(), ticket);
+  if (qi != s->queue.end()) s->queue.erase(qi);
+  s->reqs.erase(it);
+  s->cancelled++;
   s->cv.notify_one();
   return QL_OK;
 }

@@ -39,6 +39,7 @@ struct TsqrProblem {
   ColSource<S> src;  // columns of X (or of [A b])
   int64_t m;         // rows
   int n;             // columns (<= NC)
+  int vec16;         // every column starts 16-byte aligned (16-byte copies)
 };
 
 // Workspace views for one R-tree.
@@ -49,15 +50,25 @@ struct TreeView {
   int leaves;      // number of leaves (CTAs contributing a triangle)
 };
 
+// Arity of the R-tree for NC columns: for narrow X a merge costs little arithmetic and each
+// tree level mostly costs its synchronisation (an arrival counter, L2 round trips), so wide
+// nodes cut the levels; for wide X a merge costs O(n^3) FP64 per child and binary nodes
+// keep that on fewer CTAs in sequence.
+template <int NC>
+constexpr int tree_arity() {
+  return NC <= 8 ? 16 : (NC <= 16 ? 4 : 2);
+}
+
 template <int NC, int TC, int RPT, int T>
 struct TsqrShape {
   static constexpr int TR = T / TC;        // row threads per column group
   static constexpr int NCT = NC / TC;      // columns held by one thread
   static constexpr int B = TR * RPT;       // rows per tile
-  // staging depth: one buffer (the next tile lands while the current one is factored from
-  // registers).  Deeper staging was measured slower for narrow X: the extra shared memory
-  // costs CTAs per SM, and with them the latency hiding that more stages would add.
-  static constexpr int STAGES = 1;
+  // staging depth: for wide X one buffer (the next tile lands while the current one is
+  // factored from registers; the factorisation is long enough to cover the copy, and more
+  // shared memory would cost CTAs per SM).  Very narrow X factors a tile quickly, so two
+  // tiles stay in flight.
+  static constexpr int STAGES = NC <= 4 ? 2 : 1;
   static_assert(NC % TC == 0, "column groups must divide NC");
   static_assert(TR % 16 == 0 || TR == T, "row threads per group must be a multiple of 16");
 };
@@ -69,7 +80,7 @@ struct TsqrSmem {
   using V = typename Ar::T;
   static constexpr size_t kStage = sizeof(S) * NC * Sh::B;           // one staged tile
   static constexpr size_t kStages = kStage * Sh::STAGES;
-  static constexpr size_t kMerge = sizeof(double) * 2 * NC * NC;     // [Ra; Rb]
+  static constexpr size_t kMerge = sizeof(double) * tree_arity<NC>() * NC * NC;  // [Ra; Rb_1..Rb_{A-1}]
   static constexpr size_t kArena = kStages > kMerge ? kStages : kMerge;
   static constexpr size_t kR = (sizeof(typename Ar::RT) * NC * NC + 15) / 16 * 16;  // running triangle (carried type)
   static constexpr size_t kPart = sizeof(V) * NC * Sh::TR;           // column partial sums
@@ -157,6 +168,28 @@ struct TsqrCta {
   QL_DEV void issue_tile(const TsqrProblem<S>& p, int64_t row0, int buf = 0) {
     constexpr int PER = B / T > 0 ? B / T : 1;
     S* st = stage + (size_t)buf * NC * B;
+    if (p.vec16) {  // 16-byte copies; the rows past m are zero-filled
+      constexpr int EPV = 16 / (int)sizeof(S);  // elements per copy
+      constexpr int NV = B / EPV;               // copies per column
+      constexpr int PERV = NV / T > 0 ? NV / T : 1;
+#pragma unroll 1
+      for (int c = 0; c < NC; ++c) {
+        const S* col = p.src.col(c < p.n ? c : 0);
+        const bool cvalid = c < p.n;
+#pragma unroll
+        for (int e = 0; e < PERV; ++e) {
+          const int v = tid + e * T;
+          if (NV % T == 0 || v < NV) {
+            const int64_t row = row0 + (int64_t)v * EPV;
+            const int64_t left = cvalid ? p.m - row : 0;
+            const int bytes = left <= 0 ? 0 : (left >= EPV ? 16 : (int)left * (int)sizeof(S));
+            cp_async_16(st + c * B + v * EPV, bytes > 0 ? col + row : col, bytes);
+          }
+        }
+      }
+      cp_async_commit();
+      return;
+    }
 #pragma unroll 1
     for (int c = 0; c < NC; ++c) {
       const S* col = p.src.col(c < p.n ? c : 0);
@@ -367,16 +400,17 @@ struct TsqrCta {
 };
 
 // ---------------------------------------------------------------------------------------
-// FP64 merge of two triangles [Ra; Rb] -> Ra (n x n each, in shared memory, ld NC).
-// Column j's reflector touches Ra(j, :) and Rb(0..j, :) (Rb stays upper triangular in
-// its untouched part).  T threads, one column each per step.
+// FP64 merge of stacked triangles: Ra <- R of [Ra; Rb_0; ...; Rb_{nb-1}] (n x n upper
+// triangles in shared memory, ld NC; the Rb follow each other, NC x NC apart).  Column j's
+// reflector touches Ra(j, :) and rows 0..j of every Rb (their untouched parts stay upper
+// triangular), so nb + 1 triangles merge in n column steps, not nb n.  One thread per
+// trailing column; remainders below kTauF64 of their column's norm are treated as rounding
+// residue (no reflector), as in the tile factorisation.
 // ---------------------------------------------------------------------------------------
-// Remainders below kTauF64 of their column's norm are treated as rounding residue (no
-// reflector), as in the tile factorisation.
 constexpr double kTauF64Sq = 0x1p-92;  // (2^-46)^2
 
 template <int NC, int T>
-QL_DEV void merge_pair_f64(double* Ra, double* Rb, int n, double* sd) {
+QL_DEV void merge_stack_f64(double* Ra, double* Rbs, int nb, int n, double* sd) {
   int tid = threadIdx.x;
   double* cnm = sd + NC;  // sum over finished rows i < j of Ra(i, c)^2
   for (int c = tid; c < NC; c += T) cnm[c] = 0.0;
@@ -385,7 +419,10 @@ QL_DEV void merge_pair_f64(double* Ra, double* Rb, int n, double* sd) {
     double x1 = Ra[j * NC + j];
     for (int c = j + tid; c < n; c += T) {
       double s = 0.0;
-      for (int i = 0; i <= j; ++i) s = fma(Rb[i * NC + j], Rb[i * NC + c], s);
+      for (int b = 0; b < nb; ++b) {
+        const double* Rb = Rbs + (size_t)b * NC * NC;
+        for (int i = 0; i <= j; ++i) s = fma(Rb[i * NC + j], Rb[i * NC + c], s);
+      }
       sd[c] = s;
     }
     __syncthreads();
@@ -402,7 +439,10 @@ QL_DEV void merge_pair_f64(double* Ra, double* Rb, int n, double* sd) {
         double rn = fma(-v1, f, Ra[j * NC + c]);
         Ra[j * NC + c] = rn;
         cnm[c] = fma(rn, rn, cnm[c]);
-        for (int i = 0; i <= j; ++i) Rb[i * NC + c] = fma(-Rb[i * NC + j], f, Rb[i * NC + c]);
+        for (int b = 0; b < nb; ++b) {
+          double* Rb = Rbs + (size_t)b * NC * NC;
+          for (int i = 0; i <= j; ++i) Rb[i * NC + c] = fma(-Rb[i * NC + j], f, Rb[i * NC + c]);
+        }
       }
       if (tid == 0) Ra[j * NC + j] = beta;
     } else {
@@ -428,11 +468,16 @@ QL_DEV void store_tri(double* dst, const double* src, int n) {
   }
 }
 
-// Climb the binary R-tree from leaf `leaf` whose triangle is already in slot(0, leaf).
-// Returns true in exactly one CTA (the root owner), with the final triangle in Ra (smem,
-// ld NC).  Slots of level l start at sum_{l' < l} width_l'; counters likewise.
-template <int NC, int T>
-QL_DEV bool climb_tree(const TreeView& tv, int leaf, int n, double* Ra, double* Rb, double* sd, int* s_flag) {
+// Climb the A-ary R-tree from leaf `leaf`, whose triangle is already in slot(0, leaf).
+// Node i of a level has the children A i .. A i + A - 1 of the level below; the last child
+// CTA to arrive (one arrival counter per node) merges all of them and carries the result
+// up.  Returns true in exactly one CTA (the root owner), with the final triangle in Ra
+// (shared, ld NC).  `arena` holds Ra followed by room for A - 1 more triangles.  Slots of
+// level l start at sum_{l' < l} width_l'; counters at sum_{l' < l} width_{l' + 1}.
+template <int NC, int T, int A>
+QL_DEV bool climb_tree(const TreeView& tv, int leaf, int n, double* arena, double* sd, int* s_flag) {
+  double* Ra = arena;
+  double* Rbs = arena + NC * NC;
   __syncthreads();  // the leaf slot was written by all threads of this CTA
   int width = tv.leaves, idx = leaf;
   size_t slot_base = 0, cnt_base = 0;
@@ -442,34 +487,31 @@ QL_DEV bool climb_tree(const TreeView& tv, int leaf, int n, double* Ra, double* 
     return true;
   }
   while (width > 1) {
-    int parent = idx >> 1;
-    bool pair = (2 * parent + 1) < width;
-    size_t next_slot_base = slot_base + width;
-    int next_width = (width + 1) >> 1;
-    double* my_slot = tv.slots + (slot_base + (size_t)idx) * (size_t)n * n;
-    if (pair) {
+    const int parent = idx / A, first = parent * A;
+    const int cnt = min(A, width - first);
+    const int next_width = (width + A - 1) / A;
+    if (cnt > 1) {
       __threadfence();
       __syncthreads();
       if (threadIdx.x == 0) {
         int old = atomicAdd(&tv.counters[cnt_base + parent], 1);
         *s_flag = old;
-        if (old == 1) tv.counters[cnt_base + parent] = 0;  // reset for the next call
+        if (old == cnt - 1) tv.counters[cnt_base + parent] = 0;  // reset for the next call
       }
       __syncthreads();
-      if (*s_flag == 0) return false;  // sibling merges
+      if (*s_flag != cnt - 1) return false;  // a sibling merges
       __threadfence();
-      const double* a = tv.slots + (slot_base + 2 * (size_t)parent) * (size_t)n * n;
-      const double* b = a + (size_t)n * n;
-      load_tri<NC, T>(Ra, a, n);
-      load_tri<NC, T>(Rb, b, n);
+      const double* c0 = tv.slots + (slot_base + (size_t)first) * (size_t)n * n;
+      load_tri<NC, T>(Ra, c0, n);
+      for (int b = 1; b < cnt; ++b) load_tri<NC, T>(Rbs + (size_t)(b - 1) * NC * NC, c0 + (size_t)b * n * n, n);
       __syncthreads();
-      merge_pair_f64<NC, T>(Ra, Rb, n, sd);
+      merge_stack_f64<NC, T>(Ra, Rbs, cnt - 1, n, sd);
     } else {
-      load_tri<NC, T>(Ra, my_slot, n);
+      load_tri<NC, T>(Ra, tv.slots + (slot_base + (size_t)idx) * (size_t)n * n, n);
       __syncthreads();
     }
-    cnt_base += (size_t)(width >> 1);
-    slot_base = next_slot_base;
+    cnt_base += (size_t)next_width;
+    slot_base += (size_t)width;
     width = next_width;
     idx = parent;
     if (width > 1) {
@@ -480,18 +522,19 @@ QL_DEV bool climb_tree(const TreeView& tv, int leaf, int n, double* Ra, double* 
   return true;
 }
 
-// Tree sizes for `leaves` leaves: total slots and counters.
-inline size_t tree_slots(int leaves) {
+// Tree sizes for `leaves` leaves and arity A: total slots and counters.  Arity 2 bounds
+// every larger arity (the workspace is sized with it).
+inline size_t tree_slots(int leaves, int A = 2) {
   size_t s = 0;
-  for (int w = leaves; ; w = (w + 1) >> 1) {
+  for (int w = leaves;; w = (w + A - 1) / A) {
     s += (size_t)w;
     if (w <= 1) break;
   }
   return s;
 }
-inline size_t tree_counters(int leaves) {
+inline size_t tree_counters(int leaves, int A = 2) {
   size_t s = 0;
-  for (int w = leaves; w > 1; w = (w + 1) >> 1) s += (size_t)(w >> 1);
+  for (int w = leaves; w > 1; w = (w + A - 1) / A) s += (size_t)((w + A - 1) / A);
   return s + 1;
 }
 

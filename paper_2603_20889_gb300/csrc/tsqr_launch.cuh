@@ -54,8 +54,7 @@ __global__ void __launch_bounds__(T, 1) tsqr_kernel(TsqrArgs<S> a) {
     __stcg(slot + i, r <= c ? Ar::r_to_double(cta.R[r * NC + c]) : 0.0);
   }
   double* Ra = cta.arena;
-  double* Rb = cta.arena + NC * NC;
-  if (!climb_tree<NC, T>(a.tv, bid, n, Ra, Rb, cta.sd, &cta.misc[1])) return;
+  if (!climb_tree<NC, T, tree_arity<NC>()>(a.tv, bid, n, cta.arena, cta.sd, &cta.misc[1])) return;
 
   // root: every CTA has passed its range check and its tree arrival by now
   __threadfence();
@@ -95,6 +94,12 @@ ql_status launch_one(const TsqrCall& c, const TreeView& tv_in, int gated) {
   a.p.src.nA = c.nA;
   a.p.m = c.m;
   a.p.n = c.n;
+  {
+    auto al16 = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15u) == 0; };
+    bool v = al16(c.A) && ((size_t)c.lda * sizeof(S)) % 16 == 0;
+    if (c.nA < c.n) v = v && al16(c.b);
+    a.p.vec16 = v ? 1 : 0;
+  }
   a.tv = tv_in;
   a.tv.leaves = (int)g;
   a.tiles = tiles;
@@ -136,9 +141,9 @@ ql_status dispatch(const TsqrCall& c, const TreeView& tv, int gated) {
       }
     }
   }
-  if (n <= 1) return launch_one<1, 1, 32, 128, S, Ar>(c, tv, gated);
-  if (n <= 2) return launch_one<2, 1, 32, 128, S, Ar>(c, tv, gated);
-  if (n <= 4) return launch_one<4, 1, 16, 128, S, Ar>(c, tv, gated);
+  if (n <= 1) return launch_one<1, 1, 16, 128, S, Ar>(c, tv, gated);
+  if (n <= 2) return launch_one<2, 1, 16, 128, S, Ar>(c, tv, gated);
+  if (n <= 4) return launch_one<4, 1, 8, 128, S, Ar>(c, tv, gated);
   if (n <= 8) return launch_one<8, 1, 8, 128, S, Ar>(c, tv, gated);
   if (n <= 16) return launch_one<16, 4, 16, 256, S, Ar>(c, tv, gated);
   if (n <= 32) return launch_one<32, 8, 16, 256, S, Ar>(c, tv, gated);

@@ -94,7 +94,7 @@ def lstsq_case(m: int, n: int, kappa: float, seed: int, noise: float = 1e-6, dty
     return np.asfortranarray(A.astype(dtype)), b.astype(dtype), x_star
 
 
-def conditioned_upper(n: int, kappa: float, seed: int, bits: int = 40) -> np.ndarray:
+def conditioned_upper(n: int, kappa: float, seed: int, bits: int = 36) -> np.ndarray:
     """An upper triangular R0 = T1 diag(sigma) T2 with positive diagonal, rounded to
     multiples of 2^-bits: T1, T2 unit upper triangular with off-diagonal entries uniform in
     [-1/(2n), 1/(2n)] (row sums below 1/2, so kappa(T) <= 3) and sigma the geometric
@@ -115,21 +115,37 @@ def walsh_indices(m: int, n: int, seed: int) -> np.ndarray:
     return np.sort(rng.choice(m, size=n, replace=False)).astype(np.int64)
 
 
+WALSH_MIX = 64  # Walsh columns combined into every column of the exact workload
+
+
+def walsh_mix(n: int, bits: int = 36, kappa: float = 1e4, seed: int = 0):
+    """(B, R0): B = H_64[:, K] R0, 64 x n, with H_64 the 64 x 64 Sylvester Hadamard matrix and
+    K n random distinct column indices (B^T B = 64 R0^T R0 exactly; for n >= 6 the 64 rows of
+    B are distinct sign combinations of R0's rows), R0 = conditioned_upper(n, kappa, seed, bits)."""
+    R0 = conditioned_upper(n, kappa, seed, bits)
+    K = walsh_indices(WALSH_MIX, n, seed + 1)
+    H = hadamard_columns(WALSH_MIX, WALSH_MIX)[:, K]
+    return H @ R0, R0
+
+
 def hadamard_exact_case(m: int, n: int, kappa: float, seed: int):
-    """(X, R_exact) with X = H[:, J] R0: J random distinct Hadamard columns (orthogonal, norm
-    sqrt(m), rows that look random), R0 = conditioned_upper(n, kappa).  The entries of X are
-    sums of at most n multiples of 2^-40 below 1.5 in size, exact in FP64, and X^T X =
-    m R0^T R0 exactly, so R = sqrt(m) R0 (m a power of two)."""
-    if m & (m - 1) or m < n:
-        raise ValueError("m must be a power of two and >= n")
-    R0 = conditioned_upper(n, kappa, seed)
-    J = walsh_indices(m, n, seed)
+    """(X, R_exact) with X = H[:, J] B: J = 64 random distinct columns of the m x m Sylvester
+    Hadamard matrix (orthogonal, norm sqrt(m)) and B = H_64[:, :n] R0 (walsh_mix, R0 a
+    triangle of multiples of 2^-36 below 1.5 with kappa(R0) ~ kappa).  Each entry of X is a
+    signed sum of 64 entries of B, so the rows of X take a new sign pattern almost every row
+    (values close to Gaussian, no repeated rows for m < 2^64), every partial sum is a
+    multiple of 2^-36 below 2^13, exact in FP64, and X^T X = 64 m R0^T R0 exactly: R =
+    sqrt(64 m) R0 (m a power of two, n <= 64)."""
+    if m & (m - 1) or m < WALSH_MIX or n > WALSH_MIX:
+        raise ValueError("m must be a power of two >= 64 and n <= 64")
+    B, R0 = walsh_mix(n, kappa=kappa, seed=seed)
+    J = walsh_indices(m, WALSH_MIX, seed)
     i = np.arange(m, dtype=np.int64)
     X = np.zeros((m, n), order="F")
-    for k in range(n):
+    for k in range(WALSH_MIX):
         h = 1.0 - 2.0 * (np.bitwise_count(i & J[k]) & 1)
-        X[:, k:] += h[:, None] * R0[k, k:][None, :]
-    return X, math.sqrt(m) * R0
+        X += h[:, None] * B[k][None, :]
+    return X, math.sqrt(WALSH_MIX * m) * R0
 
 
 # --------------------------------------------------------------------------- device
@@ -181,19 +197,21 @@ def hadamard_exact_device(m: int, n: int, kappa: float, seed: int, device="cuda"
     are exact in any order, so the device X equals the host one bit for bit."""
     import torch
 
-    R0 = conditioned_upper(n, kappa, seed)
-    J = walsh_indices(m, n, seed)
+    if m & (m - 1) or m < WALSH_MIX or n > WALSH_MIX:
+        raise ValueError("m must be a power of two >= 64 and n <= 64")
+    B, R0 = walsh_mix(n, kappa=kappa, seed=seed)
+    J = walsh_indices(m, WALSH_MIX, seed)
     i = torch.arange(m, device=device, dtype=torch.int64)
     Xt = torch.zeros((n, m), dtype=torch.float64, device=device)
-    R0d = torch.from_numpy(R0).to(device)
-    for k in range(n):
+    Bd = torch.from_numpy(np.ascontiguousarray(B)).to(device)
+    for k in range(WALSH_MIX):
         b = i & int(J[k])
         for sh in (32, 16, 8, 4, 2, 1):  # parity of popcount(i & J_k)
             b = b ^ (b >> sh)
         h = 1.0 - 2.0 * (b & 1).to(torch.float64)
-        Xt[k:, :] += R0d[k, k:].unsqueeze(1) * h.unsqueeze(0)
+        Xt += Bd[k].unsqueeze(1) * h.unsqueeze(0)
         del b, h
-    return Xt, math.sqrt(m) * R0
+    return Xt, math.sqrt(WALSH_MIX * m) * R0
 
 
 # --------------------------------------------------------------------------- batched / serving

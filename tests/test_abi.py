@@ -89,6 +89,7 @@ int main(void) {
   printf("ql_problem %zu\nql_request %zu\nql_result %zu\nql_stats %zu\n", sizeof(ql_problem),
          sizeof(ql_request), sizeof(ql_result), sizeof(ql_stats));
   O(ql_problem, X); O(ql_problem, dtype); O(ql_problem, b); O(ql_problem, info);
+  O(ql_problem, method_hint); O(ql_problem, kappa_hint); O(ql_request, method_hint);
   O(ql_request, kappa_hint); O(ql_result, R); O(ql_stats, hbm_peak_bytes);
   return 0;
 }
@@ -109,6 +110,9 @@ int main(void) {
     assert got["ql_problem.dtype"] == q.Problem.dtype.offset
     assert got["ql_problem.b"] == q.Problem.b.offset
     assert got["ql_problem.info"] == q.Problem.info.offset
+    assert got["ql_problem.method_hint"] == q.Problem.method_hint.offset
+    assert got["ql_problem.kappa_hint"] == q.Problem.kappa_hint.offset
+    assert got["ql_request.method_hint"] == q.Request.method_hint.offset
     assert got["ql_request.kappa_hint"] == q.Request.kappa_hint.offset
     assert got["ql_result.R"] == q.Result.R.offset
     assert got["ql_stats.hbm_peak_bytes"] == q.Stats.hbm_peak_bytes.offset

@@ -219,3 +219,39 @@ def test_server_completes_when_the_budget_is_the_limit():
         s, r = srv.poll(t)
         assert s == 0 and r.status == 0
     srv.close()
+
+
+def test_server_cancel_withdraws_queued_requests_only():
+    """A client that gives up (host-side injection: it cancels its tickets) withdraws the
+    requests still queued; launched ones complete normally, and the rest of the stream is
+    unaffected."""
+    import paper_2603_20889_gb300 as q
+
+    m_big, n_big = 1 << 23, 64  # tens of ms of work: keeps the only slot busy while the rest queue
+    Xb = torch.randn((n_big, m_big), dtype=torch.float64, device="cuda")
+    m, n = 4096, 8
+    X = torch.randn((n, m), dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    srv = q.Server(8 << 30, 1, 1)  # one request in flight at a time
+    first = srv.submit(q.Request(m=m_big, n=n_big, ld=m_big, X=Xb.data_ptr(), dtype=q.QL_F64, kind=0, b=None,
+                                 kappa_hint=1.0))
+    rest = [srv.submit(q.Request(m=m, n=n, ld=m, X=X.data_ptr(), dtype=q.QL_F64, kind=0, b=None, kappa_hint=1.0))
+            for _ in range(6)]
+    L = srv.lib
+    cancelled = rest[1::2]
+    for t in cancelled:
+        assert L.ql_server_cancel(srv.h, t) == q.QL_OK
+        assert L.ql_server_cancel(srv.h, t) == q.QL_ERR_UNKNOWN  # the ticket is gone
+    assert srv.drain(60.0) == 0
+    s, r = srv.poll(first)
+    assert s == 0 and r.status == 0
+    assert L.ql_server_cancel(srv.h, first) == q.QL_ERR_BUSY  # done: poll and release instead
+    for t in rest:
+        s, r = srv.poll(t)
+        if t in cancelled:
+            assert s == q.QL_ERR_UNKNOWN
+        else:
+            assert s == 0 and r.status == 0
+    st = srv.stats()
+    assert st.completed == 1 + len(rest) - len(cancelled)
+    srv.close()

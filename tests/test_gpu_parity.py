@@ -1,9 +1,11 @@
 """GPU parity: the CUDA path (through the C ABI) against the CPU oracle, element by element.
 
-Bar: ||R - R_ref||_F / ||R_ref||_F <= 1e-13 * n * kappa(X) for FP64 TSQR;
-Cholesky-QR2 and SVQB2 are held to the same bound for kappa <= 1e6.  Sizes span several
-row tiles per CTA and ragged tails; both the double-float default and the native FP64
-arithmetic are checked.
+Bar: ||R - R_ref||_F / ||R_ref||_F <= 1e-13 * n * kappa(X) for FP64 TSQR, and the same
+bound row by row (every entry against its row's diagonal, oracle.row_err), which a wrong
+small row at large kappa cannot pass; Cholesky-QR2 and SVQB2 are held to the same bounds for
+kappa <= 1e6.  Sizes span several row tiles per CTA (at least three per CTA for every
+column class of the TSQR kernels) and ragged tails; both the double-float default and the
+native FP64 arithmetic are checked.
 """
 import functools
 
@@ -46,8 +48,28 @@ TSQR_CASES = [
 ]
 
 
+# At least three row tiles per CTA for every column class of the TSQR kernel (tile rows B,
+# CTAs per SM at the kernel's registers and shared memory): n <= 2: B = 2048, up to 4
+# CTAs/SM; n <= 4: 1024, up to 4; n <= 8: 1024, 2; n <= 16: 1024, 1; n <= 32: 512, 1;
+# n <= 64: 256, 1 -- m >= 3 x 152 x CTAs/SM x B, plus a ragged tail of 17 rows.
+MULTI_TILE_CASES = [
+    (3 * 304 * 4096 + 17, 1, 1.0), (3 * 304 * 4096 + 17, 2, 1e2), (3 * 304 * 2048 + 17, 4, 1e3),
+    (3 * 304 * 1024 + 17, 7, 1e4), (3 * 152 * 1024 + 17, 9, 1e3), (3 * 152 * 1024 + 17, 16, 1e4),
+    (3 * 152 * 512 + 17, 17, 1e3), (3 * 152 * 512 + 17, 32, 1e4), (3 * 152 * 256 + 17, 33, 1e2),
+    (3 * 152 * 256 + 17, 64, 1e3),
+]
+
+
 def _arith(q, a):
     q.set_arith(q.QL_ARITH_DF if a == "df" else q.QL_ARITH_F64)
+
+
+def check_r(R, R_ref, n, kappa):
+    """The parity bound, normwise and row by row."""
+    tol = oracle.tolerance(n, kappa)
+    err, rerr = oracle.rel_err(R, R_ref), oracle.row_err(R, R_ref)
+    assert err <= tol, ("frobenius", err, tol)
+    assert rerr <= tol, ("row-scaled", rerr, tol)
 
 
 @pytest.mark.parametrize("arith", ARITHS)
@@ -61,8 +83,39 @@ def test_tsqr_matches_oracle(m, n, kappa, arith):
     R = to_host(R)
     assert info_of(info) == [0, 0]
     assert np.all(np.tril(R, -1) == 0.0) and np.all(np.diag(R) >= 0.0)
-    err = oracle.rel_err(R, R_ref)
-    assert err <= oracle.tolerance(n, kappa), (err, oracle.tolerance(n, kappa))
+    check_r(R, R_ref, n, kappa)
+
+
+@pytest.mark.parametrize("arith", ARITHS)
+@pytest.mark.parametrize("m,n,kappa", MULTI_TILE_CASES)
+def test_tsqr_multi_tile_per_cta(m, n, kappa, arith):
+    """Every CTA folds at least three row tiles into its running triangle (the carry of R
+    across tiles and the one-tile-ahead staging), in every column class."""
+    import paper_2603_20889_gb300 as q
+
+    _arith(q, arith)
+    X, R_ref = case(m, n, kappa, n + 101)
+    R, info = q.tsqr_qless(to_dev(X))
+    R = to_host(R)
+    assert info_of(info) == [0, 0]
+    check_r(R, R_ref, n, kappa)
+
+
+@pytest.mark.parametrize("arith", ARITHS)
+@pytest.mark.parametrize("n", [1, 8, 16, 33, 64])
+def test_exact_walsh_workload(n, arith):
+    """X = H[:, J] H_64[:, K] R0 is exact in FP64 with R = sqrt(64 m) R0: every method against
+    the exact R (no oracle rounding in the reference)."""
+    import paper_2603_20889_gb300 as q
+
+    _arith(q, arith)
+    m, kappa = 1 << 18, 1e4
+    X, R_exact = synth.hadamard_exact_case(m, n, kappa, seed=n + 5)
+    Xd = to_dev(X)
+    for fn in (q.tsqr_qless, q.cholqr2_qless, lambda x: q.svqb_qless(x)[::2]):
+        R, info = fn(Xd)
+        assert info_of(info) == [0, 0]
+        check_r(to_host(R), R_exact, n, kappa)
 
 
 @pytest.mark.parametrize("method", ["cholqr2", "svqb2"])
@@ -82,8 +135,7 @@ def test_gram_methods_match_oracle(m, n, kappa, arith, method):
         R, _, info = q.svqb_qless(to_dev(X))
     R = to_host(R)
     assert info_of(info) == [0, 0]
-    err = oracle.rel_err(R, R_ref)
-    assert err <= oracle.tolerance(n, kappa), (err, oracle.tolerance(n, kappa))
+    check_r(R, R_ref, n, kappa)
 
 
 @pytest.mark.parametrize("arith", ARITHS)
@@ -281,8 +333,8 @@ def test_hadamard_exact(m, n, method):
     assert oracle.rel_err(to_host(R), R_exact) <= oracle.tolerance(n, kappa)
 
 
-@pytest.mark.parametrize("method", ["tsqr", "cholqr2"])
-@pytest.mark.parametrize("m,n,kappa", [(50001, 8, 1e2), (20000, 31, 1e4), (4097, 3, 1.0)])
+@pytest.mark.parametrize("method", ["tsqr", "cholqr2", "svqb2"])
+@pytest.mark.parametrize("m,n,kappa", [(50001, 8, 1e2), (20000, 31, 1e4), (4097, 3, 1.0), (30000, 64, 1e3)])
 def test_fp32_storage(m, n, kappa, method):
     """FP32-stored X: parity with the oracle on the float-rounded X widened to double
     (the kernel's arithmetic), and the stated storage error against the FP64 X."""
@@ -291,11 +343,11 @@ def test_fp32_storage(m, n, kappa, method):
     X64, R64 = case(m, n, kappa, 11)
     X32 = X64.astype(np.float32)
     R_ref32 = oracle.householder_r(X32.astype(np.float64))
-    fn = q.tsqr_qless if method == "tsqr" else q.cholqr2_qless
+    fn = {"tsqr": q.tsqr_qless, "cholqr2": q.cholqr2_qless, "svqb2": lambda x: q.svqb_qless(x)[::2]}[method]
     R, info = fn(to_dev(X32))
     R = to_host(R)
     assert info_of(info) == [0, 0]
-    assert oracle.rel_err(R, R_ref32) <= oracle.tolerance(n, kappa)
+    check_r(R, R_ref32, n, kappa)
     # storage error: bounded by kappa * 2^-24 (rounding X to float)
     assert oracle.rel_err(R, R64) <= 10 * n * kappa * 2.0 ** -24
 
@@ -326,6 +378,25 @@ def test_range_fallback_recomputes_in_fp64(scale):
         R, info = fn(to_dev(X * scale))
         assert info_of(info) == [0, 0]
         assert oracle.rel_err(to_host(R) / scale, R_ref) <= oracle.tolerance(7, 1e2)
+
+
+@pytest.mark.parametrize("lm,e", [(28, 50), (26, 50)])
+def test_range_guard_accounts_for_m(lm, e):
+    """A constant column x = 1.875 2^e: its entries sit inside the double-float range, but the
+    running norm sqrt(m) |x| and the Gram entry m x^2 do not once m is large; the range check
+    must send the call to FP64, which gives R = sqrt(m) x = 1.875 2^(e + lm/2) exactly."""
+    import paper_2603_20889_gb300 as q
+
+    q.set_arith(q.QL_ARITH_DF)
+    m = 1 << lm
+    x = torch.full((m,), 1.875 * 2.0 ** e, dtype=torch.float64, device="cuda")
+    expect = 1.875 * 2.0 ** (e + lm // 2)
+    for fn in (q.tsqr_qless, q.cholqr2_qless):
+        R, info = fn(x.unsqueeze(1))
+        assert info_of(info) == [0, 0]
+        assert abs(float(to_host(R)[0, 0]) - expect) <= 1e-13 * expect
+    del x
+    torch.cuda.empty_cache()
 
 
 def test_edge_cases():
@@ -367,16 +438,22 @@ def test_cholqr2_breakdown_reports_pivot():
     assert np.all(np.isnan(to_host(R)))
 
 
-@pytest.mark.parametrize("method", ["tsqr", "cholqr2", "scholqr3"])
-@pytest.mark.parametrize("dtype", ["f64", "f32"])
-@pytest.mark.parametrize("m", [60013, 60000])  # unaligned columns; 16-byte aligned columns (bulk tile copies)
-def test_lstsq_matches_oracle(method, dtype, m):
-    import paper_2603_20889_gb300 as q
-
+@functools.lru_cache(maxsize=None)
+def _lstsq_case(m, dtype):
     A, b, _ = synth.lstsq_case(m, 31, 1e3, seed=3)
     if dtype == "f32":
         A, b = A.astype(np.float32), b.astype(np.float32)
-    x_ref, rho_ref, Re_ref, info_ref = oracle.lstsq(A.astype(np.float64), b.astype(np.float64))
+    return (A, b) + tuple(oracle.lstsq(A.astype(np.float64), b.astype(np.float64)))
+
+
+@pytest.mark.parametrize("method", ["tsqr", "cholqr2", "scholqr3"])
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+# unaligned columns; 16-byte aligned columns (bulk tile copies); three TSQR tiles per CTA
+@pytest.mark.parametrize("m", [60013, 60000, 3 * 152 * 512 + 17])
+def test_lstsq_matches_oracle(method, dtype, m):
+    import paper_2603_20889_gb300 as q
+
+    A, b, x_ref, rho_ref, Re_ref, info_ref = _lstsq_case(m, dtype)
     assert info_ref == 0
     x, rn, Rext, info = q.lstsq_qless(to_dev(A), torch.from_numpy(b).cuda(),
                                       method={"tsqr": q.QL_TSQR, "cholqr2": q.QL_CHOLQR2,

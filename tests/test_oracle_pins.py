@@ -68,12 +68,14 @@ def test_hadamard_construction_is_exact(m, n):
 
 @pytest.mark.parametrize("m,n,kappa", [(1 << 12, 8, 1e4), (1 << 13, 16, 1e6), (1 << 12, 1, 1.0), (1 << 11, 33, 1e2)])
 def test_random_walsh_columns_give_the_exact_r(m, n, kappa):
-    """X = H[:, J] R0 with J random Hadamard columns and R0 a short-mantissa triangle: X is
-    exact in FP64 and R = sqrt(m) R0 (the full-size accuracy reference of the benchmark)."""
+    """X = H[:, J] H_64[:, K] R0 with J, K random Hadamard columns and R0 a short-mantissa
+    triangle: X is exact in FP64 and R = sqrt(64 m) R0 (the full-size accuracy reference of
+    the benchmark)."""
     X, R_exact = synth.hadamard_exact_case(m, n, kappa, seed=n + 11)
-    # H[:, J] has orthogonal columns of norm sqrt(m): the exact Gram is m R0^T R0
-    R0 = R_exact / np.sqrt(m)
-    assert np.allclose(X.T @ X, m * (R0.T @ R0), rtol=0, atol=64 * EPS * m * np.max(np.abs(R0)) ** 2 * n)
+    # both Hadamard factors have orthogonal columns: the exact Gram is 64 m R0^T R0
+    R0 = R_exact / np.sqrt(synth.WALSH_MIX * m)
+    G = synth.WALSH_MIX * m * (R0.T @ R0)
+    assert np.allclose(X.T @ X, G, rtol=0, atol=64 * EPS * np.max(np.abs(G)) * n)
     R = oracle.householder_r(X)
     k = oracle.kappa2(R_exact)
     assert k < 10 * max(kappa, 1.0)
