@@ -50,8 +50,8 @@ MEASURED_TRAFFIC_PER_ROW = {
 
 
 # FP32 instructions of one double-float (dot, update) pair of the Householder column step:
-# an accumulating product (13) and a product subtracted with renormalisation (16), lo * lo kept
-DF_INSTR_PER_PAIR = 29
+# an accumulating product (13, lo * lo kept) and a product subtracted with renormalisation (15)
+DF_INSTR_PER_PAIR = 28
 
 
 def rel_err(R, R_ref) -> float:
@@ -829,28 +829,39 @@ def run_wide(q, lib, torch, dev, stream, reps=2):
 
 def run_batched(q, lib, torch, dev, stream, count=512):
     """Uneven batch (m log-uniform in [2^10, 2^20], n in {4..48}, kappa log-uniform in
-    [1, 1e6], FP64): one persistent launch (plain and CUDA-graph replay) against a loop of
-    one TSQR launch per matrix on the same stream.  Accuracy: sampled instances against the
-    single-call results (same kernels) and the smallest against LAPACK's QR on the host."""
+    [1, 1e6], FP64), the method of each problem chosen by the library (method_hint = QL_AUTO
+    with the construction kappa as kappa_hint): the batched form (its persistent launches,
+    plain and CUDA-graph replay) against a loop of one single call per matrix with the same
+    method on the same stream, and against the all-TSQR batch.  Accuracy: sampled instances
+    against the single-call results and the smallest against LAPACK's QR on the host."""
+    import ctypes
+
     import numpy as np
 
     from paper_2603_20889_gb300 import synth
 
     insts = synth.batched_instances(count)
-    Xs, probs, outs = [], [], []
+    Xs, outs = [], []
     for it in insts:
         Xt = synth.conditioned_device(it.m, it.n, it.kappa, it.seed, device=dev)
         R = torch.empty((it.n, it.n), dtype=torch.float64, device=dev)
         info = torch.zeros(2, dtype=torch.int32, device=dev)
         Xs.append(Xt)
         outs.append((R, info))
-        probs.append(q.Problem(m=it.m, n=it.n, ld=it.m, X=Xt.data_ptr(), dtype=q.QL_F64, kind=0, b=None,
-                               R=R.data_ptr(), x=None, info=info.data_ptr()))
-    arr = (q.Problem * count)(*probs)
-    nb = lib.ql_batch_workspace_bytes(count, arr)
-    ws = torch.empty(nb, dtype=torch.uint8, device=dev)
+
+    def plan(hint):
+        probs = [q.Problem(m=it.m, n=it.n, ld=it.m, X=Xt.data_ptr(), dtype=q.QL_F64, kind=0, b=None,
+                           R=R.data_ptr(), x=None, info=info.data_ptr(), method_hint=hint, kappa_hint=it.kappa)
+                 for it, Xt, (R, info) in zip(insts, Xs, outs)]
+        arr = (q.Problem * count)(*probs)
+        nb = lib.ql_batch_workspace_bytes(count, arr)
+        ws = torch.empty(nb, dtype=torch.uint8, device=dev)
+        assert lib.ql_batch_prepare(count, arr, ws.data_ptr(), nb, q._stream_ptr(stream)) == 0
+        meth = (ctypes.c_int32 * count)()
+        assert lib.ql_batch_methods(ws.data_ptr(), meth, count) == 0
+        return ws, list(meth)
+
     sptr = q._stream_ptr(stream)
-    assert lib.ql_batch_prepare(count, arr, ws.data_ptr(), nb, sptr) == 0
     total_bytes = sum(8.0 * it.m * it.n for it in insts)
 
     def timed(fn, reps):
@@ -864,6 +875,10 @@ def run_batched(q, lib, torch, dev, stream, count=512):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / reps
 
+    ws_t, _ = plan(q.QL_TSQR)
+    ms_tsqr = timed(lambda: lib.ql_batch_launch(ws_t.data_ptr(), sptr), 5)
+    del ws_t
+    ws, methods = plan(q.QL_AUTO)
     ms_batch = timed(lambda: lib.ql_batch_launch(ws.data_ptr(), sptr), 5)
     side = torch.cuda.Stream(device=dev)  # capture needs a non-default stream
     side.wait_stream(stream)
@@ -874,12 +889,13 @@ def run_batched(q, lib, torch, dev, stream, count=512):
     ms_graph = timed(g.replay, 5)
     Rb = [o[0].clone() for o in outs]
     bad = [i for i, o in enumerate(outs) if o[1].cpu().tolist() != [0, 0]]
-    wsl = torch.empty(lib.ql_workspace_bytes(q.QL_TSQR, 1 << 20, 48, q.QL_F64), dtype=torch.uint8, device=dev)
+    wsl = torch.empty(lib.ql_workspace_bytes(q.QL_AUTO, 1 << 20, 48, q.QL_F64), dtype=torch.uint8, device=dev)
 
-    def loop():
-        for it, Xt, (R, info) in zip(insts, Xs, outs):
-            lib.ql_tsqr_qless(it.m, it.n, Xt.data_ptr(), q.QL_F64, it.m, R.data_ptr(), it.n, info.data_ptr(),
-                              wsl.data_ptr(), wsl.numel(), sptr)
+    def loop():  # the same method per matrix, one single call each
+        for it, Xt, (R, info), mth in zip(insts, Xs, outs, methods):
+            fn = lib.ql_cholqr2_qless if mth == q.QL_CHOLQR2 else lib.ql_tsqr_qless
+            fn(it.m, it.n, Xt.data_ptr(), q.QL_F64, it.m, R.data_ptr(), it.n, info.data_ptr(), wsl.data_ptr(),
+               wsl.numel(), sptr)
 
     ms_loop = timed(loop, 2)
     # batched vs single-call parity on a sample, and the smallest instances against LAPACK's
@@ -896,23 +912,31 @@ def run_batched(q, lib, torch, dev, stream, count=512):
         Xh = Xs[i].double().cpu().numpy().T
         Rh = Rb[i].cpu().numpy().T  # stored column-major
         worst_lapack = max(worst_lapack, rel_err(Rh, lapack_r(Xh)) / tolerance(it.n, max(it.kappa, 10.0)))
+    n_gram = sum(1 for m in methods if m == q.QL_CHOLQR2)
     del Xs
     return {
         "workload": f"{count} uneven FP64 problems: m log-uniform in [2^10, 2^20], n in {{4..48}}, "
                     "kappa log-uniform in [1, 1e6]",
-        "method": "Householder TSQR, one persistent launch (+ gated FP64 launch)",
+        "method": "per problem (method_hint = QL_AUTO, kappa_hint = construction kappa): TSQR problems in one "
+                  "persistent launch, Cholesky-QR2 problems in grouped persistent Gram launches per column class "
+                  "and pass, gated FP64 TSQR redo launch",
+        "methods_chosen": {"tsqr": count - n_gram, "cholqr2": n_gram},
+        "methods_per_instance": "".join("C" if m == q.QL_CHOLQR2 else "T" for m in methods),
         "solves_per_s_batched": round(count / (ms_batch / 1e3), 1),
         "solves_per_s_graph": round(count / (ms_graph / 1e3), 1),
         "solves_per_s_loop": round(count / (ms_loop / 1e3), 1),
+        "solves_per_s_batched_all_tsqr": round(count / (ms_tsqr / 1e3), 1),
         "speedup_vs_loop": round(ms_loop / ms_graph, 2),
         "ms_batched": round(ms_batch, 3), "ms_graph": round(ms_graph, 3), "ms_loop": round(ms_loop, 3),
+        "ms_batched_all_tsqr": round(ms_tsqr, 3),
         "eff_gbs_batched": round(total_bytes / (ms_graph / 1e3) / 1e9, 1),
+        "eff_gbs_loop": round(total_bytes / (ms_loop / 1e3) / 1e9, 1),
         "status_errors": len(bad), "max_err_over_tol_vs_single": round(worst, 4),
         "max_err_over_tol_vs_lapack": round(worst_lapack, 4),
     }
 
 
-def run_serving(q, lib, torch, dev, count=20000, rate=2000.0, budget=60 << 30, max_wall=60.0):
+def run_serving(q, lib, torch, dev, count=20000, rate=2000.0, budget=60 * 10 ** 9, max_wall=60.0):
     """Poisson stream of Q-less QR / least-squares requests through the continuous-batching
     server.  Payloads are views of device-resident pools (one 2^22 x 65 matrix per kappa
     bucket, FP64 and FP32 copies), so no host->device copy happens after arrival."""
@@ -943,7 +967,8 @@ def run_serving(q, lib, torch, dev, count=20000, rate=2000.0, budget=60 << 30, m
         el = 8 if r.dtype == "f64" else 4
         req = q.Request(m=r.m, n=r.n, ld=M, X=base, dtype=q.QL_F64 if r.dtype == "f64" else q.QL_F32,
                         kind=1 if r.kind == "lstsq" else 0,
-                        b=base + 64 * M * el if r.kind == "lstsq" else None, kappa_hint=r.kappa)
+                        b=base + 64 * M * el if r.kind == "lstsq" else None, kappa_hint=r.kappa,
+                        method_hint=q.QL_AUTO)
         tickets.append((srv.submit(req), r, b))
         submitted += 1
     t_sub = time.perf_counter() - t0
@@ -976,10 +1001,46 @@ def run_serving(q, lib, torch, dev, count=20000, rate=2000.0, budget=60 << 30, m
         Ra = Ra.cpu().numpy()
         worst = max(worst, rel_err(Rs, Ra) / tolerance(n1, max(r.kappa, 10.0)))
     srv.close()
+    # the same request list as one plain call per request, back to back on one stream (the
+    # method the batch plan would pick: Cholesky-QR2 from 24 columns at kappa <= 1e6)
+    nloop = min(len(tickets), 2000)
+    wsl = torch.empty(lib.ql_workspace_bytes(q.QL_AUTO, M, 64, q.QL_F64), dtype=torch.uint8, device=dev)
+    Rl = torch.empty(65 * 65, dtype=torch.float64, device=dev)
+    xl = torch.empty(66, dtype=torch.float64, device=dev)
+    infl = torch.zeros(2, dtype=torch.int32, device=dev)
+    sp = q._stream_ptr(torch.cuda.current_stream())
+
+    def one(r, b):
+        pool = pools64[b] if r.dtype == "f64" else pools32[b]
+        dt = q.QL_F64 if r.dtype == "f64" else q.QL_F32
+        el = 8 if r.dtype == "f64" else 4
+        ncols = r.n + (1 if r.kind == "lstsq" else 0)
+        meth = q.QL_CHOLQR2 if (ncols >= 24 and r.kappa <= 1e6) else q.QL_TSQR
+        if r.kind == "lstsq":
+            lib.ql_lstsq_qless(r.m, r.n, pool.data_ptr(), M, pool.data_ptr() + 64 * M * el, dt, meth, xl.data_ptr(),
+                               xl[r.n:].data_ptr(), None, infl.data_ptr(), wsl.data_ptr(), wsl.numel(), sp)
+        elif meth == q.QL_CHOLQR2:
+            lib.ql_cholqr2_qless(r.m, r.n, pool.data_ptr(), dt, M, Rl.data_ptr(), r.n, infl.data_ptr(), wsl.data_ptr(),
+                                 wsl.numel(), sp)
+        else:
+            lib.ql_tsqr_qless(r.m, r.n, pool.data_ptr(), dt, M, Rl.data_ptr(), r.n, infl.data_ptr(), wsl.data_ptr(),
+                              wsl.numel(), sp)
+
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for tk, r, b in tickets[:nloop]:
+        one(r, b)
+    e1.record()
+    torch.cuda.synchronize()
+    loop_sps = nloop / (e0.elapsed_time(e1) / 1e3)
     del pools64, pools32
     return {
         "workload": f"Poisson {rate:.0f} req/s, m log-uniform in [2^12, 2^22], n in {{2..64}}, 30% FP32, "
-                    "20% least squares, kappa log-uniform in [1, 1e6], 60 GiB (64.4 GB) budget",
+                    "20% least squares, kappa log-uniform in [1, 1e6] (kappa_hint, method_hint = QL_AUTO), "
+                    f"{budget / 1e9:.0f} GB budget",
+        "loop_solves_per_s": round(loop_sps, 1),
+        "loop": f"the first {nloop} requests as one plain call each, back to back, same methods",
         "submitted": submitted, "completed": int(st.completed), "offered_s": round(t_sub, 2),
         "wall_s": round(t_all, 2), "solves_per_s": round(st.completed / max(t_all, 1e-9), 1),
         "p50_ms": round(st.p50_ms, 3), "p99_ms": round(st.p99_ms, 3), "mean_ms": round(st.mean_ms, 3),

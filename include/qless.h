@@ -245,12 +245,18 @@ typedef struct {
 } ql_problem;
 
 /*
- * Many uneven problems in ONE persistent launch (Householder TSQR for every problem).
- * probs: HOST array of `count` problems.  The batch plan (work list, per-problem R-tree
- * counters and leaf slots) lives in `ws` (ql_batch_workspace_bytes); the host-side
- * plan is rebuilt on every call.  Row-block height and CTA count come from the built-in
- * autotune table (ql_autotune).  Equivalent, problem by problem, to ql_tsqr_qless /
- * ql_lstsq_qless up to rounding order.
+ * Many uneven problems, each by its own method (Householder TSQR, Sec. 3.2, or
+ * Cholesky-QR2, Sec. 3.1, Algorithm 1).  probs: HOST array of `count` problems.  The method
+ * of a problem is its method_hint, or for QL_AUTO the autotune table entry of its
+ * (m, n, dtype, kappa) class (ql_autotune), else Cholesky-QR2 from 24 columns when
+ * 0 < kappa_hint <= 1e6 and TSQR otherwise; the Gram method needs n (+1 for least squares)
+ * >= 9, narrower problems always run TSQR.  All TSQR problems run in ONE persistent launch
+ * (work list of row-tile chunks, per-problem R-trees); the Cholesky-QR2 problems run as
+ * work items of one persistent launch per (column class, storage, pass) of the
+ * tensor-core Gram kernels.  A problem that leaves the double-float range, or (QL_AUTO)
+ * whose Cholesky breaks down, is redone by a final gated FP64 TSQR launch.  The plan lives
+ * in `ws` (ql_batch_workspace_bytes) and is rebuilt on every call.  Equivalent, problem by
+ * problem, to the single-call entry points up to rounding order.
  */
 size_t ql_batch_workspace_bytes(int32_t count, const ql_problem* probs);
 ql_status ql_batch_qless(int32_t count, const ql_problem* probs, void* ws, size_t ws_bytes, void* stream);
@@ -262,6 +268,9 @@ ql_status ql_batch_qless(int32_t count, const ql_problem* probs, void* ws, size_
  * graph and replayed (the first launch of the process should happen before capture). */
 ql_status ql_batch_prepare(int32_t count, const ql_problem* probs, void* ws, size_t ws_bytes, void* stream);
 ql_status ql_batch_launch(void* ws, void* stream);
+/* The method chosen for each problem of the plan last prepared in `ws` (QL_TSQR or
+ * QL_CHOLQR2, in the caller's order; count must equal the batch's).  Host only. */
+ql_status ql_batch_methods(void* ws, int32_t* methods, int32_t count);
 
 /*
  * Autotuner: times the candidate configurations (rows per CTA tile, CTAs per SM, method)

@@ -54,6 +54,7 @@ SIGNATURES = {
     "ql_batch_qless": (_i32, [_i32, _vp, _vp, _sz, _vp]),
     "ql_batch_prepare": (_i32, [_i32, _vp, _vp, _sz, _vp]),
     "ql_batch_launch": (_i32, [_vp, _vp]),
+    "ql_batch_methods": (_i32, [_vp, _vp, _i32]),
     "ql_autotune_workspace_bytes": (_sz, [_i64, _i64, _i32]),
     "ql_autotune": (_i32, [_i64, _i64, _i32, _f64, _vp, _sz, _vp, _vp, _vp]),
     "ql_autotune_save": (_i32, [ctypes.c_char_p]),

@@ -53,7 +53,7 @@ size_t ql_workspace_bytes(ql_method method, int64_t m, int64_t n, ql_dtype dtype
   size_t t = tsqr_workspace_bytes((int)(n + 1 <= kApiMaxN ? n + 1 : n));
   size_t g = gram_workspace_bytes((int)(n + 1 <= kApiMaxN ? n + 1 : n));
   switch (method) {
-    case QL_TSQR: return t;
+    case QL_TSQR: return n == 1 && g > t ? g : t;  // n = 1 runs the one-column streaming pass
     case QL_CHOLQR2:
     case QL_SCHOLQR3:
     case QL_SVQB2: return g;
@@ -67,6 +67,27 @@ ql_status ql_tsqr_qless(int64_t m, int64_t n, const void* X, ql_dtype dtype, int
   ql_status st = check_matrix(m, n, X, dtype, ldx, kApiMaxN);
   if (st) return st;
   if ((st = check_r(R, ldr, n))) return st;
+  if (n == 1) {
+    // one column: R = ||x||, the norm that the Householder reflector of x is built from,
+    // streamed by the one-column Gram pass (no tiles, reflectors or R-tree needed)
+    GramCall g;
+    g.m = m;
+    g.n = 1;
+    g.nA = 1;
+    g.A = X;
+    g.lda = ldx;
+    g.b = X;
+    g.dtype = dtype;
+    g.method = QL_TSQR;
+    g.epilogue = kEpiR;
+    g.R = R;
+    g.ldr = ldr;
+    g.info = info;
+    g.ws = ws;
+    g.ws_bytes = ws_bytes;
+    g.stream = (cudaStream_t)stream;
+    return gram_launch(g, current_arith());
+  }
   TsqrCall c;
   c.m = m;
   c.n = (int)n;
@@ -83,7 +104,12 @@ ql_status ql_tsqr_qless(int64_t m, int64_t n, const void* X, ql_dtype dtype, int
   c.ws_bytes = ws_bytes;
   c.stream = (cudaStream_t)stream;
   int ctas = 0;
-  if (tune_lookup(m, n, dtype, 1.0, nullptr, &ctas)) c.ctas_per_sm = ctas;
+  int var = -1, ar = 0;
+  if (tune_lookup(m, n, dtype, 1.0, nullptr, &ctas, &var, &ar)) {
+    c.ctas_per_sm = ctas;
+    c.variant = var;
+    c.arity = ar;
+  }
   return tsqr_launch(c, current_arith());
 }
 

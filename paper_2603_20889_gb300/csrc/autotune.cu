@@ -1,11 +1,15 @@
 // Project autotuner: for an (m, n, dtype, kappa) class it times the candidate
-// configurations on the current GPU -- TSQR with 1 or 2 CTAs per SM (which sets the
-// number of R-tree leaves and the rows per CTA; a request above what the registers allow
-// is clamped, so for n > 8, one CTA per SM, both are the same launch) and Cholesky-QR2
-// when the condition hint allows it (kappa <= 1e6, where the Gram method stays within the
-// accuracy bound) -- and records the fastest in a process-wide table that
-// ql_autotune_choose() and the QL_AUTO paths consult.  The table persists as a small JSON
-// text file.
+// configurations on the current GPU and records the fastest in a process-wide table that
+// the single-call entry points, ql_autotune_choose() and the batched form consult:
+//   * TSQR: CTAs per SM (1, 2, and 4 for n <= 4 -- it sets the R-tree leaves and the rows
+//     per CTA; a request above what registers and shared memory allow is clamped), the
+//     row-block height (for n > 8 three thread layouts of the tile kernel: 16 rows x 4
+//     columns per thread at 256 threads, 8 rows x 4 columns at 256 threads, 8 rows x 8
+//     columns at 128 threads, i.e. tiles of 256/128/128 rows at n = 64) and the R-tree
+//     arity (binary, or the wide default of narrow X);
+//   * Cholesky-QR2, when the condition hint allows it (kappa <= 1e6, where the Gram method
+//     stays within the accuracy bound).
+// The table persists as a small JSON text file.
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -14,6 +18,7 @@
 #include <mutex>
 #include <string>
 #include <tuple>
+#include <vector>
 
 #include "internal.h"
 
@@ -28,6 +33,8 @@ struct TuneKey {
 struct TuneVal {
   int method;  // QL_TSQR or QL_CHOLQR2
   int ctas_per_sm;
+  int variant;  // TSQR thread layout (row-block height), 0 = default
+  int arity;    // TSQR R-tree arity, 0 = default
   double ms;
 };
 
@@ -40,12 +47,15 @@ static TuneKey key_of(int64_t m, int64_t n, ql_dtype dt, double kappa) {
   return TuneKey{(int)dt, (int)n, ml, kappa > 1e6 ? 1 : 0};
 }
 
-bool tune_lookup(int64_t m, int64_t n, ql_dtype dt, double kappa, int* method, int* ctas) {
+bool tune_lookup(int64_t m, int64_t n, ql_dtype dt, double kappa, int* method, int* ctas, int* variant,
+                 int* arity) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
   auto it = g_tune.find(key_of(m, n, dt, kappa));
   if (it == g_tune.end()) return false;
   if (method) *method = it->second.method;
   if (ctas) *ctas = it->second.ctas_per_sm;
+  if (variant) *variant = it->second.variant;
+  if (arity) *arity = it->second.arity;
   return true;
 }
 
@@ -99,12 +109,17 @@ ql_status ql_autotune(int64_t m, int64_t n, ql_dtype dtype, double kappa_hint, v
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   struct Cand {
-    int method, ctas;
+    int method, ctas, variant, arity;
   };
-  Cand cands[3] = {{QL_TSQR, 1}, {QL_TSQR, 2}, {QL_CHOLQR2, 0}};
-  int ncand = kappa_hint > 1e6 ? 2 : 3;
-  TuneVal best{QL_TSQR, 0, 1e30};
-  for (int ci = 0; ci < ncand; ++ci) {
+  std::vector<Cand> cands;
+  const int ctas_opts[3] = {1, 2, 4};
+  const int nvar = (n > 8 && dtype == QL_F64) ? 3 : 1;
+  for (int ci = 0; ci < (n <= 4 ? 3 : 2); ++ci)
+    for (int v = 0; v < nvar; ++v)
+      for (int ar : {0, 2}) cands.push_back(Cand{QL_TSQR, ctas_opts[ci], v, ar});
+  if (kappa_hint <= 1e6 && n > 1) cands.push_back(Cand{QL_CHOLQR2, 0, 0, 0});
+  TuneVal best{QL_TSQR, 0, 0, 0, 1e30};
+  for (size_t ci = 0; ci < cands.size(); ++ci) {
     auto run = [&]() -> ql_status {
       if (cands[ci].method == QL_TSQR) {
         TsqrCall c;
@@ -122,6 +137,8 @@ ql_status ql_autotune(int64_t m, int64_t n, ql_dtype dtype, double kappa_hint, v
         c.ws_bytes = swsb;
         c.stream = st;
         c.ctas_per_sm = cands[ci].ctas;
+        c.variant = cands[ci].variant;
+        c.arity = cands[ci].arity;
         return tsqr_launch(c, current_arith());
       }
       return ql_cholqr2_qless(m, n, X, dtype, m, R, n, info, sws, swsb, stream);
@@ -138,7 +155,8 @@ ql_status ql_autotune(int64_t m, int64_t n, ql_dtype dtype, double kappa_hint, v
       cudaEventElapsedTime(&ms, e0, e1);
       if (ms < best_ms) best_ms = ms;
     }
-    if (best_ms < best.ms) best = TuneVal{cands[ci].method, cands[ci].ctas, best_ms};
+    if (best_ms < best.ms)
+      best = TuneVal{cands[ci].method, cands[ci].ctas, cands[ci].variant, cands[ci].arity, best_ms};
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -154,7 +172,7 @@ ql_status ql_autotune(int64_t m, int64_t n, ql_dtype dtype, double kappa_hint, v
 
 ql_method ql_autotune_choose(int64_t m, int64_t n, ql_dtype dtype, double kappa_hint) {
   int method = QL_TSQR;
-  if (tune_lookup(m, n, dtype, kappa_hint, &method, nullptr)) return method;
+  if (tune_lookup(m, n, dtype, kappa_hint, &method, nullptr, nullptr, nullptr)) return method;
   // model: Householder TSQR reads X once and is stable for every kappa
   return QL_TSQR;
 }
@@ -167,9 +185,11 @@ ql_status ql_autotune_save(const char* path) {
   std::fprintf(f, "{\"arch\": \"sm_103a\", \"entries\": [");
   bool first = true;
   for (auto& e : g_tune) {
-    std::fprintf(f, "%s\n {\"dtype\": %d, \"n\": %d, \"mlog2\": %d, \"kbucket\": %d, \"method\": %d, \"ctas\": %d, \"ms\": %.6f}",
+    std::fprintf(f,
+                 "%s\n {\"dtype\": %d, \"n\": %d, \"mlog2\": %d, \"kbucket\": %d, \"method\": %d, \"ctas\": %d, "
+                 "\"variant\": %d, \"arity\": %d, \"ms\": %.6f}",
                  first ? "" : ",", e.first.dtype, e.first.n, e.first.mlog2, e.first.kbucket, e.second.method,
-                 e.second.ctas_per_sm, e.second.ms);
+                 e.second.ctas_per_sm, e.second.variant, e.second.arity, e.second.ms);
     first = false;
   }
   std::fprintf(f, "\n]}\n");
@@ -193,10 +213,15 @@ ql_status ql_autotune_load(const char* path) {
     TuneKey key{};
     TuneVal val{};
     if (std::sscanf(s.c_str() + pos,
-                    "{\"dtype\": %d, \"n\": %d, \"mlog2\": %d, \"kbucket\": %d, \"method\": %d, \"ctas\": %d, \"ms\": %lf}",
-                    &key.dtype, &key.n, &key.mlog2, &key.kbucket, &val.method, &val.ctas_per_sm, &val.ms) == 7) {
-      g_tune[key] = val;
-      ++loaded;
+                    "{\"dtype\": %d, \"n\": %d, \"mlog2\": %d, \"kbucket\": %d, \"method\": %d, \"ctas\": %d, "
+                    "\"variant\": %d, \"arity\": %d, \"ms\": %lf}",
+                    &key.dtype, &key.n, &key.mlog2, &key.kbucket, &val.method, &val.ctas_per_sm, &val.variant,
+                    &val.arity, &val.ms) == 9) {
+      if ((val.method == QL_TSQR || val.method == QL_CHOLQR2) && val.ctas_per_sm >= 0 && val.variant >= 0 &&
+          val.variant <= 2 && (val.arity == 0 || (val.arity >= 2 && val.arity <= 64))) {
+        g_tune[key] = val;
+        ++loaded;
+      }
     }
     pos += 8;
   }

@@ -1,31 +1,45 @@
-// Batched Q-less TSQR: many uneven problems in ONE persistent launch.
+// Batched Q-less QR: many uneven problems, each by the method chosen for it.
 //
-// The host plan splits every problem into chunks of row tiles (the leaves of that
-// problem's R-tree) and orders the problems by decreasing work.  A fixed grid of
-// persistent CTAs claims chunks through one atomic counter; a CTA factors its chunk with
-// the single-problem tile machinery (tsqr.cuh) of the problem's column class, stores the
-// leaf triangle and climbs that problem's tree; whoever completes a root writes R (or the
-// least-squares solution).  Problems whose data leave the double-float range are redone
-// by a second, gated FP64 launch that only touches flagged problems.
+// Method per problem: the caller's method_hint, or for QL_AUTO the autotune table entry of
+// its (m, n, dtype, kappa) class, else a model (Cholesky-QR2 from 24 columns when
+// 0 < kappa_hint <= 1e6, where the tensor-core Gram passes outrun the Householder tiles;
+// TSQR otherwise).  The Gram method covers n >= 9 (tensor-core kernels); narrower problems
+// always run TSQR.
+//
+// TSQR problems run in ONE persistent launch.  The host plan splits every problem into
+// chunks of row tiles (the leaves of that problem's R-tree) and orders the problems by
+// decreasing work.  A fixed grid of persistent CTAs claims chunks through one atomic
+// counter; a CTA factors its chunk with the single-problem tile machinery (tsqr.cuh) of
+// the problem's column class, stores the leaf triangle and climbs that problem's tree;
+// whoever completes a root writes R (or the least-squares solution).
+//
+// Cholesky-QR2 problems run as work items of grouped persistent Gram launches, one per
+// (column class, storage, pass) (batch_gram.cu).  Stream order: the Gram first passes, the
+// TSQR launch, the Gram second passes, then a gated FP64 TSQR launch that redoes every
+// flagged problem -- TSQR problems whose data leave the double-float range, and Gram
+// problems that left it or (method chosen automatically) whose Cholesky broke down.
 #include <algorithm>
+#include <cstddef>
 #include <cstring>
 #include <mutex>
 #include <vector>
 
+#include "batch_gram.h"
 #include "epilogue.cuh"
 #include "internal.h"
 #include "tsqr.cuh"
 
 namespace ql {
 
-// Column classes of the batched kernel: NC, TC, RPT at T = 128 threads.
+// Column classes of the batched TSQR kernel: NC, TC, RPT at T = 256 threads (for n > 8 the
+// layouts of the single-call kernel, measured fastest there).
 template <int NC> struct BatchCls;
-template <> struct BatchCls<4> { static constexpr int TC = 1, RPT = 16; };
+template <> struct BatchCls<4> { static constexpr int TC = 1, RPT = 8; };
 template <> struct BatchCls<8> { static constexpr int TC = 1, RPT = 8; };
-template <> struct BatchCls<16> { static constexpr int TC = 2, RPT = 8; };
-template <> struct BatchCls<32> { static constexpr int TC = 4, RPT = 8; };
-template <> struct BatchCls<64> { static constexpr int TC = 8, RPT = 8; };
-constexpr int kBatchT = 128;
+template <> struct BatchCls<16> { static constexpr int TC = 4, RPT = 16; };
+template <> struct BatchCls<32> { static constexpr int TC = 8, RPT = 16; };
+template <> struct BatchCls<64> { static constexpr int TC = 16, RPT = 16; };
+constexpr int kBatchT = 256;
 
 static int class_of(int n) { return n <= 4 ? 4 : n <= 8 ? 8 : n <= 16 ? 16 : n <= 32 ? 32 : 64; }
 template <int NC>
@@ -61,13 +75,17 @@ struct BatchItem {
   double* x;
   int32_t* info;
   int flag_idx;
+  int method;  // QL_TSQR, or QL_CHOLQR2 (TSQR items of such problems run only when flagged)
 };
 
+constexpr int kMaxGramGroups = 6;  // column classes 16, 32, 64 x storage F64, F32
 struct BatchHeader {
   int work_counter[2];  // [0] double-float launch, [1] gated FP64 launch
   int count;
   int pad;
-  int64_t total_work;
+  int64_t total_work;     // chunks of every problem (the gated FP64 launch)
+  int64_t total_work_df;  // chunks of the TSQR problems, which come first
+  int gram_counter[2 * kMaxGramGroups];  // per group and pass
 };
 
 template <int NC, typename S, typename Ar>
@@ -107,7 +125,7 @@ QL_DEV void batch_chunk(const BatchItem& it, int64_t chunk, unsigned char* smem,
     __stcg(slot + i, r <= c ? Ar::r_to_double(cta.R[r * NC + c]) : 0.0);
   }
   double* Ra = cta.arena;
-  if (!climb_tree<NC, T, tree_arity<NC>()>(tv, (int)chunk, n, cta.arena, cta.sd, &cta.misc[1])) return;
+  if (!climb_tree<NC, T>(tv, (int)chunk, n, cta.arena, cta.sd, &cta.misc[1], tree_arity<NC>())) return;
   __threadfence();
   if (Ar::kRangeChecked && *(volatile int*)&flags[it.flag_idx] != 0) return;
   if (it.kind == 0)
@@ -137,7 +155,7 @@ __global__ void __launch_bounds__(kBatchT, 1)
   __shared__ int64_t s_work;
   __shared__ int s_item;
   if (gated && *(volatile int*)&flags[-1] == 0) return;  // no problem left the range
-  const int64_t total = hdr->total_work;
+  const int64_t total = gated ? hdr->total_work : hdr->total_work_df;
   for (;;) {
     if (threadIdx.x == 0) {
       s_work = atomicAdd(&hdr->work_counter[gated ? 1 : 0], 1);
@@ -166,16 +184,17 @@ __global__ void __launch_bounds__(kBatchT, 1)
   }
 }
 
+template <int NC, typename S, typename Ar>
+static size_t cls_smem() {
+  return TsqrSmem<NC, BatchCls<NC>::TC, BatchCls<NC>::RPT, kBatchT, S, Ar>::kBytes;
+}
 template <typename Ar>
 static size_t batch_smem_bytes() {
   size_t b = 0;
-  b = std::max(b, TsqrSmem<4, 1, 16, kBatchT, float, Ar>::kBytes);
-  b = std::max(b, TsqrSmem<64, 8, 8, kBatchT, float, Ar>::kBytes);
-  b = std::max(b, TsqrSmem<4, 1, 16, kBatchT, double, Ar>::kBytes);
-  b = std::max(b, TsqrSmem<8, 1, 8, kBatchT, double, Ar>::kBytes);
-  b = std::max(b, TsqrSmem<16, 2, 8, kBatchT, double, Ar>::kBytes);
-  b = std::max(b, TsqrSmem<32, 4, 8, kBatchT, double, Ar>::kBytes);
-  b = std::max(b, TsqrSmem<64, 8, 8, kBatchT, double, Ar>::kBytes);
+  b = std::max({b, cls_smem<4, float, Ar>(), cls_smem<8, float, Ar>(), cls_smem<16, float, Ar>(),
+                cls_smem<32, float, Ar>(), cls_smem<64, float, Ar>()});
+  b = std::max({b, cls_smem<4, double, Ar>(), cls_smem<8, double, Ar>(), cls_smem<16, double, Ar>(),
+                cls_smem<32, double, Ar>(), cls_smem<64, double, Ar>()});
   return b;
 }
 
@@ -183,34 +202,70 @@ static size_t batch_smem_bytes() {
 // Host plan
 // ---------------------------------------------------------------------------------------
 
+struct GramGroupPlan {
+  int nc = 0, dtype = 0;
+  std::vector<GramGroupItem> items;
+  int64_t total = 0;
+  size_t off_items = 0;
+};
+
 struct BatchPlan {
-  std::vector<BatchItem> items;
-  size_t off_items = 0, off_flags = 0, off_counters = 0, off_slots = 0, bytes = 0;
-  int64_t total_work = 0;
+  std::vector<BatchItem> items;        // TSQR plan of every problem, TSQR problems first
+  std::vector<int32_t> method;         // chosen method per problem, in the caller's order
+  std::vector<GramGroupPlan> groups;   // Cholesky-QR2 problems by (column class, storage)
+  size_t off_items = 0, off_flags = 0, off_counters = 0, off_gflags = 0, off_slots = 0, off_gram = 0,
+         off_groups = 0, bytes = 0;
+  int64_t total_work = 0, total_work_df = 0;
+  size_t gram_flag_blocks = 0;  // Gram problems (512-byte flag block each, zeroed per launch)
 };
 
 // Tiles per chunk: aim for chunks of about kTargetRows rows (fewer, longer chunks for
 // wide problems keep their FP64 tree merges cheap), overridable by the tuner.
 static int64_t g_target_rows = 1 << 15;
 
-static bool make_plan(int32_t count, const ql_problem* probs, BatchPlan& P) {
-  P.items.clear();
+static int gram_class_of(int ncols) { return ncols <= 8 ? 0 : ncols <= 16 ? 16 : ncols <= 32 ? 32 : 64; }
+
+// The method of one problem (see the file comment).
+static int choose_method(const ql_problem& pr, int ncols) {
+  if (gram_class_of(ncols) == 0 || !tc_gram_enabled() || current_arith() == QL_ARITH_F64) return QL_TSQR;
+  if (pr.method_hint == QL_CHOLQR2) return QL_CHOLQR2;
+  if (pr.method_hint != QL_AUTO) return QL_TSQR;
+  int m = QL_TSQR;
+  if (tune_lookup(pr.m, ncols, pr.dtype, pr.kappa_hint > 0.0 ? pr.kappa_hint : 1e300, &m, nullptr))
+    return m == QL_CHOLQR2 ? QL_CHOLQR2 : QL_TSQR;
+  return (pr.kappa_hint > 0.0 && pr.kappa_hint <= 1e6 && ncols >= 24) ? QL_CHOLQR2 : QL_TSQR;
+}
+
+// Build the plan; with `ws` non-null the Gram items' device pointers point into it.
+static bool make_plan(int32_t count, const ql_problem* probs, BatchPlan& P, unsigned char* ws = nullptr) {
+  P = BatchPlan();
+  P.method.assign(count, QL_TSQR);
+  for (int i = 0; i < count; ++i) {
+    const ql_problem& pr = probs[i];
+    if (pr.m < 0 || pr.n < 1 || pr.n > 64 || (pr.kind == 1 && pr.n > 63)) return false;
+    if (pr.ld < (pr.m > 1 ? pr.m : 1) || (pr.dtype != QL_F64 && pr.dtype != QL_F32)) return false;
+    if (!pr.R || (pr.kind == 1 && (!pr.x || !pr.b)) || (pr.m > 0 && !pr.X)) return false;
+    P.method[i] = choose_method(pr, (int)pr.n + (pr.kind == 1 ? 1 : 0));
+  }
   std::vector<int> order(count);
   for (int i = 0; i < count; ++i) order[i] = i;
   auto work = [&](int i) { return (double)probs[i].m * probs[i].n * probs[i].n; };
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work(a) > work(b); });
+  // TSQR problems first (the double-float TSQR launch covers a prefix of the work list),
+  // each part by decreasing work
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    const bool ta = P.method[a] == QL_TSQR, tb = P.method[b] == QL_TSQR;
+    if (ta != tb) return ta;
+    return work(a) > work(b);
+  });
   // chunk height: the batch's rows split into at least ~4 chunks per persistent CTA
   // (so a small batch still fills the GPU), between 2048 rows and g_target_rows
   int64_t total_rows = 0;
   for (int i = 0; i < count; ++i) total_rows += probs[i].m > 0 ? probs[i].m : 0;
-  const int64_t ctas = (int64_t)device_sm_count() * 2;
+  const int64_t ctas = (int64_t)device_sm_count();
   const int64_t target = std::max<int64_t>(2048, std::min<int64_t>(g_target_rows, total_rows / (4 * ctas)));
   int64_t slots = 0, cnts = 0, wb = 0;
   for (int k = 0; k < count; ++k) {
     const ql_problem& pr = probs[order[k]];
-    if (pr.m < 0 || pr.n < 1 || pr.n > 64 || (pr.kind == 1 && pr.n > 63)) return false;
-    if (pr.ld < (pr.m > 1 ? pr.m : 1) || (pr.dtype != QL_F64 && pr.dtype != QL_F32)) return false;
-    if (!pr.R || (pr.kind == 1 && (!pr.x || !pr.b)) || (pr.m > 0 && !pr.X)) return false;
     BatchItem it{};
     it.A = pr.X;
     it.b = pr.kind == 1 ? pr.b : pr.X;
@@ -232,6 +287,7 @@ static bool make_plan(int32_t count, const ql_problem* probs, BatchPlan& P) {
     it.tiles_per_chunk = tpc;
     it.work_begin = wb;
     wb += it.chunks;
+    if (P.method[order[k]] == QL_TSQR) P.total_work_df = wb;
     it.slot_off = slots;
     slots += (int64_t)tree_slots(it.chunks) * it.n * it.n;
     it.cnt_off = cnts;
@@ -240,6 +296,7 @@ static bool make_plan(int32_t count, const ql_problem* probs, BatchPlan& P) {
     it.x = pr.x;
     it.info = pr.info;
     it.flag_idx = k;
+    it.method = P.method[order[k]];
     P.items.push_back(it);
   }
   P.total_work = wb;
@@ -250,8 +307,89 @@ static bool make_plan(int32_t count, const ql_problem* probs, BatchPlan& P) {
   off += ((count + 1) * sizeof(int) + 255) / 256 * 256;
   P.off_counters = off;
   off += (cnts * sizeof(int) + 255) / 256 * 256;
+  // Gram problems: flag blocks (cleared with the counters), then carried blocks, partials
+  // and FP64 accumulator blocks, then the group item arrays
+  P.off_gflags = off;
+  std::vector<int> gram_probs;
+  for (int k = 0; k < count; ++k)
+    if (P.items[k].method == QL_CHOLQR2) gram_probs.push_back(k);
+  P.gram_flag_blocks = gram_probs.size();
+  off += gram_probs.size() * 512;
   P.off_slots = off;
-  off += slots * sizeof(double);
+  off += ((size_t)slots * sizeof(double) + 255) / 256 * 256;
+  P.off_gram = off;
+  int gidx[3][2];
+  for (auto& r : gidx) r[0] = r[1] = -1;
+  int fb = 0;
+  for (int k : gram_probs) {
+    const BatchItem& it = P.items[k];
+    const int nc = gram_class_of(it.n), ci = nc == 16 ? 0 : (nc == 32 ? 1 : 2), di = it.dtype == QL_F64 ? 0 : 1;
+    if (gidx[ci][di] < 0) {
+      gidx[ci][di] = (int)P.groups.size();
+      P.groups.emplace_back();
+      P.groups.back().nc = nc;
+      P.groups.back().dtype = it.dtype;
+    }
+    GramGroupPlan& G = P.groups[gidx[ci][di]];
+    const int KT = gram_group_tile_rows(nc);
+    const int64_t tiles = (it.m + KT - 1) / KT;
+    const int64_t tpc = std::max<int64_t>(1, target / KT);
+    const int nch = (int)std::max<int64_t>(1, std::min<int64_t>(4096, (tiles + tpc - 1) / tpc));
+    GramGroupItem gi{};
+    GramArgs<double>& a = gi.args;
+    const size_t keep_b = ((size_t)3 * nc * nc * sizeof(double) + 255) / 256 * 256;
+    const size_t part_b = (size_t)nch * nc * nc * sizeof(double);
+    const size_t fbuf_b = nc == 64 ? (size_t)nch * 64 * 128 * sizeof(double) : 0;
+    const size_t flags_off = P.off_gflags + (size_t)fb * 512, keep_off = off, part_off = off + keep_b,
+                 fbuf_off = off + keep_b + part_b;
+    off += keep_b + part_b + fbuf_b;
+    ++fb;
+    auto at = [&](size_t o) { return ws ? ws + o : nullptr; };
+    a.src.A = static_cast<const double*>(it.A);
+    a.src.lda = it.lda;
+    a.src.b = static_cast<const double*>(it.b);
+    a.src.nA = it.nA;
+    a.m = it.m;
+    a.n = it.n;
+    a.tiles = tiles;
+    a.pass = 1;
+    a.method = QL_CHOLQR2;
+    a.gated = 0;
+    a.epilogue = it.kind == 1 ? kEpiLstsq : kEpiR;
+    a.w.flags = reinterpret_cast<int*>(at(flags_off));
+    a.w.keep = reinterpret_cast<double*>(at(keep_off));
+    a.w.partials = reinterpret_cast<double*>(at(part_off));
+    a.w.fbuf = reinterpret_cast<double*>(at(fbuf_off));
+    if (it.kind == 1) {  // R_ext into R (ld n + 1), x and the residual norm into x
+      a.x = it.x;
+      a.resnorm = it.x + (it.n - 1);
+      a.Rext = it.R;
+    } else {
+      a.R = it.R;
+      a.ldr = it.n;
+    }
+    a.info = it.info;
+    {
+      auto al16 = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15u) == 0; };
+      const size_t es = it.dtype == QL_F64 ? 8 : 4;
+      bool b = al16(it.A) && ((size_t)it.lda * es) % 16 == 0;
+      if (it.kind == 1) b = b && al16(it.b);
+      a.bulk = b ? 1 : 0;
+    }
+    a.mround = 2;
+    a.redo = reinterpret_cast<int*>(at(P.off_flags)) + 1 + k;
+    a.redo_any = reinterpret_cast<int*>(at(P.off_flags));
+    a.redo_on_breakdown = probs[order[k]].method_hint == QL_AUTO ? 1 : 0;
+    gi.work_begin = G.total;
+    gi.nchunks = nch;
+    G.total += nch;
+    G.items.push_back(gi);
+  }
+  P.off_groups = off = (off + 255) / 256 * 256;
+  for (auto& G : P.groups) {
+    G.off_items = off;
+    off += (G.items.size() * sizeof(GramGroupItem) + 255) / 256 * 256;
+  }
   P.bytes = off;
   return true;
 }
@@ -312,6 +450,21 @@ static PlanCache g_plans;
 void set_batch_target_rows(int64_t rows) { g_target_rows = rows < 256 ? 256 : rows; }
 int64_t batch_target_rows() { return g_target_rows; }
 
+// The host image of what the device needs of a plan: [header, TSQR items] (uploaded to
+// offset 0) followed by the Gram group item arrays (uploaded to off_groups).
+static size_t upload_bytes(const BatchPlan& P) { return P.off_flags + (P.bytes - P.off_groups); }
+static void fill_upload(const BatchPlan& P, int32_t count, unsigned char* dst) {
+  BatchHeader h{};
+  h.count = count;
+  h.total_work = P.total_work;
+  h.total_work_df = P.total_work_df;
+  std::memset(dst, 0, upload_bytes(P));
+  std::memcpy(dst, &h, sizeof(h));
+  std::memcpy(dst + P.off_items, P.items.data(), P.items.size() * sizeof(BatchItem));
+  for (const auto& G : P.groups)
+    std::memcpy(dst + P.off_flags + (G.off_items - P.off_groups), G.items.data(), G.items.size() * sizeof(GramGroupItem));
+}
+
 // Asynchronous plan upload through a caller-owned pinned staging buffer (the serving
 // loop's path: no host synchronisation).  The staging bytes must stay untouched until the
 // stream has passed the copy.
@@ -319,15 +472,16 @@ ql_status batch_prepare_async(int32_t count, const ql_problem* probs, void* ws, 
                               unsigned char* pinned, size_t pinned_bytes) {
   if (count < 1 || !probs) return QL_ERR_ARG;
   BatchPlan P;
-  if (!make_plan(count, probs, P)) return QL_ERR_ARG;
+  if (!make_plan(count, probs, P, static_cast<unsigned char*>(ws))) return QL_ERR_ARG;
   if (!ws || ws_bytes < P.bytes) return QL_ERR_WORKSPACE;
-  if (!pinned || pinned_bytes < P.off_flags) return QL_ERR_WORKSPACE;
-  BatchHeader h{};
-  h.count = count;
-  h.total_work = P.total_work;
-  std::memcpy(pinned, &h, sizeof(h));
-  std::memcpy(pinned + P.off_items, P.items.data(), P.items.size() * sizeof(BatchItem));
-  if (cudaMemcpyAsync(ws, pinned, P.off_flags, cudaMemcpyHostToDevice, st) != cudaSuccess) return QL_ERR_CUDA;
+  if (!pinned || pinned_bytes < upload_bytes(P)) return QL_ERR_WORKSPACE;
+  fill_upload(P, count, pinned);
+  unsigned char* w = static_cast<unsigned char*>(ws);
+  if (cudaMemcpyAsync(w, pinned, P.off_flags, cudaMemcpyHostToDevice, st) != cudaSuccess) return QL_ERR_CUDA;
+  if (P.bytes > P.off_groups &&
+      cudaMemcpyAsync(w + P.off_groups, pinned + P.off_flags, P.bytes - P.off_groups, cudaMemcpyHostToDevice, st) !=
+          cudaSuccess)
+    return QL_ERR_CUDA;
   g_plans.put(ws, P);
   return QL_OK;
 }
@@ -335,7 +489,7 @@ ql_status batch_prepare_async(int32_t count, const ql_problem* probs, void* ws, 
 size_t batch_plan_upload_bytes(int32_t count, const ql_problem* probs) {
   BatchPlan P;
   if (count < 1 || !probs || !make_plan(count, probs, P)) return 0;
-  return P.off_flags;
+  return upload_bytes(P);
 }
 
 }  // namespace ql
@@ -354,19 +508,17 @@ size_t ql_batch_workspace_bytes(int32_t count, const ql_problem* probs) {
 ql_status ql_batch_prepare(int32_t count, const ql_problem* probs, void* ws, size_t ws_bytes, void* stream) {
   if (count < 1 || !probs) return QL_ERR_ARG;
   BatchPlan P;
-  if (!make_plan(count, probs, P)) return QL_ERR_ARG;
+  if (!make_plan(count, probs, P, static_cast<unsigned char*>(ws))) return QL_ERR_ARG;
   if (!ws || ws_bytes < P.bytes) return QL_ERR_WORKSPACE;
   cudaStream_t st = (cudaStream_t)stream;
   unsigned char* w = static_cast<unsigned char*>(ws);
-  BatchHeader h{};
-  h.count = count;
-  h.total_work = P.total_work;
-  // pageable host sources: cudaMemcpyAsync returns once the data is staged
-  if (cudaMemcpyAsync(w, &h, sizeof(h), cudaMemcpyHostToDevice, st) != cudaSuccess) return QL_ERR_CUDA;
-  if (cudaMemcpyAsync(w + P.off_items, P.items.data(), P.items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice,
-                      st) != cudaSuccess)
+  std::vector<unsigned char> img(upload_bytes(P));
+  fill_upload(P, count, img.data());
+  if (cudaMemcpyAsync(w, img.data(), P.off_flags, cudaMemcpyHostToDevice, st) != cudaSuccess) return QL_ERR_CUDA;
+  if (P.bytes > P.off_groups && cudaMemcpyAsync(w + P.off_groups, img.data() + P.off_flags, P.bytes - P.off_groups,
+                                                cudaMemcpyHostToDevice, st) != cudaSuccess)
     return QL_ERR_CUDA;
-  if (cudaStreamSynchronize(st) != cudaSuccess) return QL_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return QL_ERR_CUDA;  // img is freed on return
   g_plans.put(ws, P);
   return QL_OK;
 }
@@ -377,13 +529,35 @@ ql_status ql_batch_launch(void* ws, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   unsigned char* w = static_cast<unsigned char*>(ws);
   const int count = (int)P.items.size();
-  // counters, flags and the work counters start at zero on every launch
-  if (cudaMemsetAsync(w, 0, 2 * sizeof(int), st) != cudaSuccess) return QL_ERR_CUDA;
+  // work counters, tree counters and every flag (TSQR and Gram) start at zero on every launch
+  if (cudaMemsetAsync(w, 0, offsetof(BatchHeader, count), st) != cudaSuccess) return QL_ERR_CUDA;
+  if (cudaMemsetAsync(w + offsetof(BatchHeader, gram_counter), 0, sizeof(int) * 2 * kMaxGramGroups, st) !=
+      cudaSuccess)
+    return QL_ERR_CUDA;
   if (cudaMemsetAsync(w + P.off_flags, 0, P.off_slots - P.off_flags, st) != cudaSuccess) return QL_ERR_CUDA;
-  ql_status s = current_arith() == QL_ARITH_F64 ? launch_batch<ArithF64>(w, P, count, st, 0)
-                                                : launch_batch<ArithDF>(w, P, count, st, 0);
-  if (s != QL_OK || current_arith() == QL_ARITH_F64) return s;
-  return launch_batch<ArithF64>(w, P, count, st, 1);
+  BatchHeader* hdr = reinterpret_cast<BatchHeader*>(w);
+  const bool f64 = current_arith() == QL_ARITH_F64;  // then every problem runs TSQR (the plan chose so)
+  ql_status s = QL_OK;
+  auto gram_pass = [&](int pass) {
+    for (size_t g = 0; g < P.groups.size() && s == QL_OK; ++g) {
+      const GramGroupPlan& G = P.groups[g];
+      s = gram_group_launch(G.nc, G.dtype, pass, &hdr->gram_counter[2 * g + pass - 1],
+                            reinterpret_cast<const GramGroupItem*>(w + G.off_items), (int)G.items.size(), G.total, st);
+    }
+  };
+  gram_pass(1);
+  if (s == QL_OK) s = f64 ? launch_batch<ArithF64>(w, P, count, st, 0) : launch_batch<ArithDF>(w, P, count, st, 0);
+  if (s == QL_OK) gram_pass(2);
+  if (s != QL_OK || f64) return s;
+  return launch_batch<ArithF64>(w, P, count, st, 1);  // flagged problems, any method
+}
+
+ql_status ql_batch_methods(void* ws, int32_t* methods, int32_t count) {
+  BatchPlan P;
+  if (!ws || !methods || !g_plans.get(ws, P)) return QL_ERR_ARG;
+  if (count != (int32_t)P.method.size()) return QL_ERR_ARG;
+  std::memcpy(methods, P.method.data(), sizeof(int32_t) * count);
+  return QL_OK;
 }
 
 ql_status ql_batch_qless(int32_t count, const ql_problem* probs, void* ws, size_t ws_bytes, void* stream) {

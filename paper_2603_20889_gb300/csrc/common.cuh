@@ -55,11 +55,12 @@ QL_DEV df df_mul(df a, df b) {
   e = __fmaf_rn(a.lo, b.hi, e);
   return df_make(p, e);
 }
-// a - b * c, one renormalisation.
+// a - b * c, one renormalisation.  Used for updates w -= v f whose b.lo * c.lo term changes
+// sign with the row (v.lo), so it is left out (it would only add cost, not remove a bias).
 QL_DEV df df_sub_mul(df a, df b, df c) {
   float p = __fmul_rn(b.hi, c.hi);
   float e = __fmaf_rn(b.hi, c.hi, -p);
-  e = __fmaf_rn(b.hi, c.lo, __fmaf_rn(b.lo, c.lo, e));
+  e = __fmaf_rn(b.hi, c.lo, e);
   e = __fmaf_rn(b.lo, c.hi, e);
   float s, t;
   two_sum(a.hi, -p, s, t);

@@ -20,8 +20,9 @@ static int nc_of(int n) { return n <= 1 ? 1 : n <= 2 ? 2 : n <= 4 ? 4 : n <= 8 ?
 static size_t gram_layout(int n, GramWs* w, void* base) {
   const int nc = nc_of(n);
   const size_t head = 512;  // flags, counters and the first pass's column exponents
-  const size_t keep = (size_t)3 * kMaxN * kMaxN * sizeof(double);
-  const size_t parts = (size_t)device_sm_count() * kGramMaxCtasPerSm * nc * nc * sizeof(double);
+  const size_t keep = ((size_t)3 * nc * nc * sizeof(double) + 255) / 256 * 256;  // 3 n x n blocks (ld n)
+  // one NC x NC partial per CTA (the streaming kernel for nc <= 4 runs up to 8 CTAs per SM)
+  const size_t parts = (size_t)device_sm_count() * (nc <= 4 ? 8 : kGramMaxCtasPerSm) * nc * nc * sizeof(double);
   // FP64 accumulators of the tcgen05 kernel (64 columns, one CTA per SM)
   const size_t fbuf = nc == 64 ? (size_t)device_sm_count() * 64 * 128 * sizeof(double) : 0;
   if (w && base) {
@@ -41,7 +42,9 @@ size_t gram_workspace_bytes(int n) {
 
 ql_status gram_launch(const GramCall& c, ql_arith arith) {
   if (c.n < 1 || c.n > kMaxN) return QL_ERR_ARG;
-  if (c.method != QL_CHOLQR2 && c.method != QL_SVQB2 && c.method != QL_SCHOLQR3) return QL_ERR_ARG;
+  if (c.method != QL_CHOLQR2 && c.method != QL_SVQB2 && c.method != QL_SCHOLQR3 &&
+      !(c.method == QL_TSQR && c.n == 1 && c.epilogue == kEpiR))
+    return QL_ERR_ARG;
   if (!c.ws || c.ws_bytes < gram_layout(c.n, nullptr, nullptr)) return QL_ERR_WORKSPACE;
   GramWs w;
   gram_layout(c.n, &w, c.ws);

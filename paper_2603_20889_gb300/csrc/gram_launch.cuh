@@ -53,7 +53,19 @@ struct GramArgs {
   // inverse of what it applies): 0 FP64 as is, 1 double-float per entry, 2 the tensor-core
   // slicing (48-bit fixed point per column of M' = diag(2^e_k) M).
   int mround;
+  // Batched form only (null otherwise): the problem's flag in the batch's gated FP64 TSQR
+  // launch, and that launch's any-flag.  A problem that leaves the double-float range (or,
+  // with redo_on_breakdown, whose Cholesky breaks down) is handed to that launch instead of
+  // the FP64 Gram launches of a single call.
+  int* redo;
+  int* redo_any;
+  int redo_on_breakdown;
 };
+
+QL_DEV void gram_request_redo(int* redo, int* redo_any) {
+  atomicOr(redo, 1);
+  atomicOr(redo_any, 1);
+}
 
 // Round the upper triangular M (n x n, row-major ld LE in shared memory) the way the next
 // pass's kernel reads it (GramArgs::mround), in place.  colexp[k] is the largest biased
@@ -111,8 +123,10 @@ QL_DEV void write_nan_outputs(const GramArgs<S>& a, int T) {
   }
 }
 
+// k: the number of CTA partials of this pass (the grid, or the chunks of one problem in a
+// grouped launch).
 template <int NC, int T, typename S, typename Ar>
-QL_DEV void gram_finish(const GramArgs<S>& a, unsigned char* smem, const int* colmax, int* misc);
+QL_DEV void gram_finish(const GramArgs<S>& a, unsigned char* smem, const int* colmax, int* misc, int k);
 
 template <int NC, typename S, typename Ar, int XF>
 __global__ void __launch_bounds__(GramShape<NC>::T, 1) gram_kernel(GramArgs<S> a) {
@@ -274,16 +288,16 @@ __global__ void __launch_bounds__(GramShape<NC>::T, 1) gram_kernel(GramArgs<S> a
     int p = pp * BS + ij / BS, q = qq * BS + ij % BS;
     __stcg(part + p * NC + q, s);
   }
-  gram_finish<NC, T, S, Ar>(a, smem, colmax, misc);
+  gram_finish<NC, T, S, Ar>(a, smem, colmax, misc, gridDim.x);
 }
 
 // Range verdict, "last CTA done" election and, in the last CTA, the fixed-order reduction
 // of all CTA partials followed by the n x n FP64 epilogue of the pass.  Shared by the SIMT
 // and the tensor-core Gram kernels (the caller has written this CTA's partial already).
 template <int NC, int T, typename S, typename Ar>
-QL_DEV void gram_finish(const GramArgs<S>& a, unsigned char* smem, const int* colmax, int* misc) {
+QL_DEV void gram_finish(const GramArgs<S>& a, unsigned char* smem, const int* colmax, int* misc, int k) {
   using V = typename Ar::T;
-  const int tid = threadIdx.x, n = a.n, k = gridDim.x;
+  const int tid = threadIdx.x, n = a.n;
   if (tid == 0) {
     bool bad = false;
     if constexpr (Ar::kRangeChecked) {
@@ -307,7 +321,10 @@ QL_DEV void gram_finish(const GramArgs<S>& a, unsigned char* smem, const int* co
   __syncthreads();
   if (!misc[0]) return;
   __threadfence();
-  if (Ar::kRangeChecked && *(volatile int*)&a.w.flags[0] != 0) return;  // the FP64 launches redo it
+  if (Ar::kRangeChecked && *(volatile int*)&a.w.flags[0] != 0) {  // the FP64 launches redo it
+    if (a.redo && tid == 0) gram_request_redo(a.redo, a.redo_any);
+    return;
+  }
 
   // ---------------- epilogue: one CTA, FP64, shared memory reused from here on; the odd
   // leading dimension keeps column walks (Jacobi rotations) free of bank conflicts
@@ -319,19 +336,39 @@ QL_DEV void gram_finish(const GramArgs<S>& a, unsigned char* smem, const int* co
   double* vec = Qs + NC * LE;  // 8 LE doubles
   int* sflag = reinterpret_cast<int*>(vec + 8 * LE);
   __syncthreads();
-  // fixed-order FP64 sum of the CTA partials (bitwise reproducible)
-  for (int e = tid; e < n * n; e += T) {
-    int p = e / n, q = e % n;
-    if (p > q) continue;
-    double v = 0.0;
-    for (int b = 0; b < k; ++b) v += __ldcg(a.w.partials + (size_t)b * NC * NC + p * NC + q);
-    Cs[p * LE + q] = v;
-    Cs[q * LE + p] = v;
+  // fixed-order FP64 sum of the CTA partials (bitwise reproducible).  P lanes share an
+  // entry (as many as the thread count allows, up to a warp): each sums a strided subset of
+  // the k partials, so the L2 loads overlap instead of forming one dependent chain of k, and
+  // shuffles combine the P sums.
+  {
+    const int ne = n * n;
+    int P = 32;
+    while (P > 1 && ne * P > T) P >>= 1;
+    const int per = T / P, iters = (ne + per - 1) / per;
+    const int li = tid % P;
+    for (int it = 0; it < iters; ++it) {
+      const int e = tid / P + it * per;
+      const int p = e / n, q = e % n;
+      const bool use = e < ne && p <= q;
+      double v = 0.0;
+      if (use)
+        for (int b = li; b < k; b += P) v += __ldcg(a.w.partials + (size_t)b * NC * NC + p * NC + q);
+      for (int o = P >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (use && li == 0) {
+        Cs[p * LE + q] = v;
+        Cs[q * LE + p] = v;
+      }
+    }
   }
   __syncthreads();
   double* keep = a.w.keep;  // [0]: R1 or S1, [1]: M (R1^{-1} or B1)
   const int nn = n * n;
-  if (a.method == QL_CHOLQR2 || a.method == QL_SCHOLQR3) {
+  if (a.method == QL_TSQR) {
+    // one column: the Householder reflector of x is determined by ||x||, so R = sqrt(x^T x)
+    // (a zero column gives R = 0, not a breakdown)
+    if (tid == 0) Ps[0] = sqrt(fmax(Cs[0], 0.0));
+    __syncthreads();
+  } else if (a.method == QL_CHOLQR2 || a.method == QL_SCHOLQR3) {
     const int last = a.method == QL_SCHOLQR3 ? 3 : 2;
     if (a.method == QL_SCHOLQR3 && a.pass == 1) {
       // shifted Cholesky: C1 + s I with s = 11 (m n + n (n + 1)) u ||X||_F^2, u = 2^-53
@@ -346,6 +383,10 @@ QL_DEV void gram_finish(const GramArgs<S>& a, unsigned char* smem, const int* co
     int fail = chol_upper_inplace<T>(Cs, LE, n, sflag);
     if (fail) {
       if (a.pass < last) a.w.flags[1] = 1;
+      if (a.redo && a.redo_on_breakdown) {  // batched, method chosen automatically: TSQR redoes it
+        if (tid == 0) gram_request_redo(a.redo, a.redo_any);
+        return;
+      }
       write_nan_outputs(a, T);
       write_info(a.info, QL_ERR_NOT_SPD, fail + 1000 * (a.pass - 1));
       return;
@@ -433,7 +474,8 @@ QL_DEV void gram_finish(const GramArgs<S>& a, unsigned char* smem, const int* co
 template <int NC>
 struct StreamShape {
   static constexpr int T = 256;
-  static constexpr int U = NC <= 2 ? 4 : (NC <= 4 ? 2 : 1);  // 16-byte loads in flight per column
+  static constexpr int U = NC <= 1 ? 8 : (NC <= 2 ? 4 : 2);  // 16-byte loads per column and batch
+  static constexpr int kMaxCtasPerSm = 8;
   static constexpr int NE = NC * (NC + 1) / 2;                 // upper-triangle entries
 };
 
@@ -505,11 +547,12 @@ __global__ void __launch_bounds__(StreamShape<NC>::T) gram_stream_kernel(GramArg
 #pragma unroll
   for (int c = 0; c < NC; ++c) col[c] = a.src.col(c < n ? c : 0);
 
-  // this CTA's rows, in 16-byte units of EPV rows
+  // this CTA's rows, in 16-byte units of EPV rows; batches of U units per thread, the next
+  // batch's loads issued before the current batch is consumed (two register buffers)
   const int64_t units = (a.m + EPV - 1) / EPV;
   const int64_t u0 = units * blockIdx.x / gridDim.x, u1 = units * (blockIdx.x + 1) / gridDim.x;
-  for (int64_t ub = u0; ub < u1; ub += (int64_t)T * U) {
-    S vals[U][NC][EPV];
+  const int64_t step = (int64_t)T * U;
+  auto load_batch = [&](S (&v)[U][NC][EPV], int64_t ub) {
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int64_t uu = ub + (int64_t)u * T + tid;
@@ -517,14 +560,16 @@ __global__ void __launch_bounds__(StreamShape<NC>::T) gram_stream_kernel(GramArg
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
         if (c < n && uu < u1 && a.bulk && row + EPV <= a.m) {
-          load16<S>(vals[u][c], col[c] + row);
+          load16<S>(v[u][c], col[c] + row);
         } else {
 #pragma unroll
           for (int e = 0; e < EPV; ++e)
-            vals[u][c][e] = (c < n && uu < u1 && row + e < a.m) ? __ldg(col[c] + row + e) : S(0);
+            v[u][c][e] = (c < n && uu < u1 && row + e < a.m) ? __ldg(col[c] + row + e) : S(0);
         }
       }
     }
+  };
+  auto consume_batch = [&](const S (&v)[U][NC][EPV]) {
 #pragma unroll
     for (int u = 0; u < U; ++u)
 #pragma unroll
@@ -533,7 +578,7 @@ __global__ void __launch_bounds__(StreamShape<NC>::T) gram_stream_kernel(GramArg
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
           int E;
-          y[c] = Ar::load(vals[u][c][e], E);
+          y[c] = Ar::load(v[u][c][e], E);
           if constexpr (Ar::kRangeChecked) emax[c] = max(emax[c], (unsigned)E);
         }
         if constexpr (XF != kXNone) {  // y = x M, one row
@@ -555,6 +600,14 @@ __global__ void __launch_bounds__(StreamShape<NC>::T) gram_stream_kernel(GramArg
 #pragma unroll
           for (int j = i; j < NC; ++j) Ar::acc_fma(acc[ei++], y[i], y[j]);
       }
+  };
+  S bufA[U][NC][EPV], bufB[U][NC][EPV];
+  if (u0 < u1) load_batch(bufA, u0);
+  for (int64_t ub = u0; ub < u1; ub += 2 * step) {
+    if (ub + step < u1) load_batch(bufB, ub + step);
+    consume_batch(bufA);
+    if (ub + 2 * step < u1) load_batch(bufA, ub + 2 * step);
+    if (ub + step < u1) consume_batch(bufB);
   }
 
   if constexpr (Ar::kRangeChecked) {
@@ -584,7 +637,7 @@ __global__ void __launch_bounds__(StreamShape<NC>::T) gram_stream_kernel(GramArg
     }
     __stcg(part + i * NC + (i + rem), v);
   }
-  gram_finish<NC, T, S, Ar>(a, smem, colmax, misc);
+  gram_finish<NC, T, S, Ar>(a, smem, colmax, misc, gridDim.x);
 }
 
 template <int NC, typename S, typename Ar, int XF>
@@ -602,7 +655,7 @@ ql_status gram_stream_launch_one(const GramCall& c, const GramWs& w, int pass, i
       int o = 0;
       if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, Sh::T, Sm::kBytes) != cudaSuccess)
         return QL_ERR_CUDA;
-      occ = o < 1 ? 1 : (o > kGramMaxCtasPerSm ? kGramMaxCtasPerSm : o);
+      occ = o < 1 ? 1 : (o > Sh::kMaxCtasPerSm ? Sh::kMaxCtasPerSm : o);
     }
   }
   constexpr int EPV = 16 / (int)sizeof(S);
@@ -644,9 +697,12 @@ ql_status gram_stream_launch_one(const GramCall& c, const GramWs& w, int pass, i
   return cudaPeekAtLastError() == cudaSuccess ? QL_OK : QL_ERR_CUDA;
 }
 
-// Tensor-core Gram pass (double-float policy only): see gram_tc.cuh.
+// Tensor-core Gram pass (double-float policy only): see gram_tc.cuh.  The body handles the
+// row tiles [tiles bid / k, tiles (bid + 1) / k) of one problem as partial `bid` of `k`; the
+// single-call kernel runs it with bid = CTA, k = grid, the grouped kernel of the batched form
+// once per (problem, chunk) work item.
 template <int NC, typename S, int XF>
-__global__ void __launch_bounds__(256, 1) gram_tc_kernel(GramArgs<S> a) {
+QL_DEV void gram_tc_body(const GramArgs<S>& a, int bid, int k) {
   using Ar = ArithDF;
   using Sh = TcShape<NC>;
   using Sm = TcSmem<NC, S>;
@@ -661,7 +717,7 @@ __global__ void __launch_bounds__(256, 1) gram_tc_kernel(GramArgs<S> a) {
 
   if (a.pass >= 2 && *(volatile int*)&a.w.flags[0] != 0) return;  // the FP64 launches redo it
   if (a.pass >= 2 && *(volatile int*)&a.w.flags[1] != 0) {         // first pass broke down
-    if (blockIdx.x == 0) write_nan_outputs(a, T);
+    if (bid == 0) write_nan_outputs(a, T);
     return;
   }
   S* stage = reinterpret_cast<S*>(smem);
@@ -737,7 +793,7 @@ __global__ void __launch_bounds__(256, 1) gram_tc_kernel(GramArgs<S> a) {
     }
     if (__syncthreads_or(bad)) {  // out of the double-float range: the FP64 launches redo it
       if (tid == 0) atomicOr(&a.w.flags[0], 1);
-      gram_finish<NC, T, S, ArithDF>(a, smem, colmax, misc);
+      gram_finish<NC, T, S, ArithDF>(a, smem, colmax, misc, k);
       return;
     }
   }
@@ -754,7 +810,6 @@ __global__ void __launch_bounds__(256, 1) gram_tc_kernel(GramArgs<S> a) {
         acc64[ui][gi][e] = 0.0;
       }
 
-  const int k = gridDim.x, bid = blockIdx.x;
   const int64_t t0 = a.tiles * bid / k, t1 = a.tiles * (bid + 1) / k;
   auto issue = [&](int64_t t) {
     const int64_t row0 = t * KT;
@@ -1010,7 +1065,12 @@ __global__ void __launch_bounds__(256, 1) gram_tc_kernel(GramArgs<S> a) {
     const int i = rb2 * 16 + (ln >> 2) + (e >= 2 ? 8 : 0), j = cbb * 8 + 2 * (ln & 3) + (e & 1);
     if (i < NC && j < NC) __stcg(part + i * NC + j, s);
   }
-  gram_finish<NC, T, S, ArithDF>(a, smem, colmax, misc);
+  gram_finish<NC, T, S, ArithDF>(a, smem, colmax, misc, k);
+}
+
+template <int NC, typename S, int XF>
+__global__ void __launch_bounds__(256, 1) gram_tc_kernel(GramArgs<S> a) {
+  gram_tc_body<NC, S, XF>(a, blockIdx.x, gridDim.x);
 }
 
 template <int NC, typename S, int XF>
@@ -1072,8 +1132,10 @@ __host__ __device__ constexpr int umma_threads() {
   return XF == kXNone ? 512 : 256;
 }
 
+// The body handles partial `bid` of `k` of one problem (see gram_tc_body) with the 512
+// tensor-memory columns at tbase that its caller allocated.
 template <int NC, typename S, int XF>
-__global__ void __launch_bounds__(umma_threads<XF>(), 1) gram_umma_kernel(GramArgs<S> a) {
+QL_DEV void gram_umma_body(const GramArgs<S>& a, int bid, int k, uint32_t tbase) {
   using Sh = UmmaShape<NC>;
   using Sm = UmmaSmem<NC, S>;
   constexpr int T = umma_threads<XF>(), NW = T / 32, KT = Sh::KT, LDS = Sm::LDS, LDY = Sm::LDY, SP = Sh::SP,
@@ -1085,12 +1147,13 @@ __global__ void __launch_bounds__(umma_threads<XF>(), 1) gram_umma_kernel(GramAr
   constexpr int HALF = NC / (NW / 4);           // accumulator columns per thread (NW / 4 warps per lane quarter)
   constexpr int CPG = KT / 8;                   // core matrices per 8-column group
   constexpr uint32_t IDESC = umma_idesc_bf16(128, NC);
-  extern __shared__ __align__(1024) unsigned char smem[];
+  extern __shared__ __align__(1024) unsigned char smem_umma[];
+  unsigned char* smem = smem_umma;
   const int tid = threadIdx.x, n = a.n, lane = tid & 31, warp = tid >> 5;
 
   if (a.pass >= 2 && *(volatile int*)&a.w.flags[0] != 0) return;  // the FP64 launches redo it
   if (a.pass >= 2 && *(volatile int*)&a.w.flags[1] != 0) {         // first pass broke down
-    if (blockIdx.x == 0) write_nan_outputs(a, T);
+    if (bid == 0) write_nan_outputs(a, T);
     return;
   }
   unsigned char* digits = smem;  // 7 planes, core-matrix layout
@@ -1103,7 +1166,6 @@ __global__ void __launch_bounds__(umma_threads<XF>(), 1) gram_umma_kernel(GramAr
   int* misc = reinterpret_cast<int*>(smem + Sm::kOffMisc);
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + Sm::kOffBar);
   uint64_t* lbar = reinterpret_cast<uint64_t*>(smem + Sm::kOffBar + 8);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + Sm::kOffBar + 16);
 
   for (int i = tid; i < NC; i += T) {
     colmax[i] = 0;
@@ -1163,13 +1225,12 @@ __global__ void __launch_bounds__(umma_threads<XF>(), 1) gram_umma_kernel(GramAr
     }
     if (__syncthreads_or(bad)) {  // out of the double-float range: the FP64 launches redo it
       if (tid == 0) atomicOr(&a.w.flags[0], 1);
-      gram_finish<NC, T, S, ArithDF>(a, smem, colmax, misc);
+      gram_finish<NC, T, S, ArithDF>(a, smem, colmax, misc, k);
       return;
     }
   }
 
-  // ---- tensor memory for the 7 accumulator blocks, and the MMA-completion barrier
-  if (warp == 0) tmem_alloc(tslot, Sh::TCOLS);
+  // ---- the MMA-completion and tile barriers (the 7 accumulator blocks live at tbase)
   if (tid == 0) {
     mbar_init(mbar, 1);
     mbar_init(lbar, 1);
@@ -1177,21 +1238,19 @@ __global__ void __launch_bounds__(umma_threads<XF>(), 1) gram_umma_kernel(GramAr
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t tbase = *tslot;
 
   const int qd = warp & 3, hh = warp >> 2;  // TMEM lane quarter and column part of this warp
   const int L = 32 * qd + lane, kq = L / NC, li = L % NC;
   df acc[HALF];
   // FP64 level of the accumulators: this CTA's [NC columns][128 lanes] block of the
   // workspace (L2-resident; each thread touches only its own entries)
-  double* fb = a.w.fbuf + (size_t)blockIdx.x * NC * 128;
+  double* fb = a.w.fbuf + (size_t)bid * NC * 128;
 #pragma unroll
   for (int j = 0; j < HALF; ++j) {
     acc[j] = df{0.0f, 0.0f};
     __stcg(fb + (size_t)(hh * HALF + j) * 128 + L, 0.0);
   }
 
-  const int k = gridDim.x, bid = blockIdx.x;
   const int64_t t0 = a.tiles * bid / k, t1 = a.tiles * (bid + 1) / k;
   // a full tile of 16-byte aligned columns arrives by bulk copies (one per column, issued by
   // one thread, completion on lbar); otherwise element by element with zero fill
@@ -1453,7 +1512,6 @@ __global__ void __launch_bounds__(umma_threads<XF>(), 1) gram_umma_kernel(GramAr
   cp_async_wait_all();  // an early exit may leave a prefetch in flight
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) tmem_dealloc(tbase, Sh::TCOLS);
   if (!ok && tid == 0) {  // the FP64 launches redo the call and report {QL_ERR_TIMEOUT, where}
     atomicCAS(&a.w.flags[4], 0, fail_where);
     atomicOr(&a.w.flags[0], 2);
@@ -1476,7 +1534,25 @@ __global__ void __launch_bounds__(umma_threads<XF>(), 1) gram_umma_kernel(GramAr
     for (int kk = 0; kk < SP; ++kk) s += red[(kk * NC + i) * NC + j];
     __stcg(part + e, s);
   }
-  gram_finish<NC, T, S, ArithDF>(a, smem, colmax, misc);
+  gram_finish<NC, T, S, ArithDF>(a, smem, colmax, misc, k);
+}
+
+template <int NC, typename S, int XF>
+__global__ void __launch_bounds__(umma_threads<XF>(), 1) gram_umma_kernel(GramArgs<S> a) {
+  using Sh = UmmaShape<NC>;
+  using Sm = UmmaSmem<NC, S>;
+  extern __shared__ __align__(1024) unsigned char smem_umma[];
+  unsigned char* smem = smem_umma;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + Sm::kOffBar + 16);
+  if ((threadIdx.x >> 5) == 0) tmem_alloc(tslot, Sh::TCOLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = *tslot;
+  gram_umma_body<NC, S, XF>(a, blockIdx.x, gridDim.x, tbase);
+  tc_fence_before();
+  __syncthreads();
+  if ((threadIdx.x >> 5) == 0) tmem_dealloc(tbase, Sh::TCOLS);
 }
 
 template <int NC, typename S, int XF>
@@ -1584,6 +1660,7 @@ ql_status gram_launch_one(const GramCall& c, const GramWs& w, int pass, int gate
 // All passes of one method (two, three for shifted Cholesky-QR3) for one (storage, arithmetic) pair.
 template <typename S, typename Ar>
 ql_status gram_dispatch(const GramCall& c, const GramWs& w, int gated) {
+  if (c.method == QL_TSQR) return gram_stream_launch_one<1, S, Ar, kXNone>(c, w, 1, gated);  // n = 1: ||x||
   auto two = [&](auto nc_tag) -> ql_status {
     constexpr int NC = decltype(nc_tag)::value;
     if constexpr (NC >= 16 && std::is_same<Ar, ArithDF>::value) {

@@ -33,6 +33,8 @@ struct TsqrCall {
   cudaStream_t stream = nullptr;
   int ctas_per_sm = 0;  // 0: occupancy maximum
   int max_ctas = 0;     // 0: no limit (testing the R-tree with few leaves)
+  int variant = -1;     // thread layout (row-block height) for n > 8: -1 environment default, 0..2
+  int arity = 0;        // R-tree arity: 0 the column class's default, else 2 .. default
 };
 
 // Upper bound of the TSQR workspace for n columns (any m).
@@ -91,8 +93,10 @@ void count_launch();
 // dst = the first nonzero {status, index} pair among src[0 .. count) (one tiny launch).
 ql_status first_status_async(int32_t* dst, const int32_t* src, int count, cudaStream_t stream);
 
-// Autotune table lookup (method, CTAs per SM) for an (m, n, dtype, kappa) class.
-bool tune_lookup(int64_t m, int64_t n, ql_dtype dt, double kappa, int* method, int* ctas);
+// Autotune table lookup for an (m, n, dtype, kappa) class: method, TSQR CTAs per SM, thread
+// layout and R-tree arity (null outputs are skipped).
+bool tune_lookup(int64_t m, int64_t n, ql_dtype dt, double kappa, int* method, int* ctas, int* variant = nullptr,
+                 int* arity = nullptr);
 
 // Batched path, asynchronous plan upload through pinned staging (serving loop).
 ql_status batch_prepare_async(int32_t count, const ql_problem* probs, void* ws, size_t ws_bytes, cudaStream_t st,

@@ -472,10 +472,11 @@ QL_DEV void store_tri(double* dst, const double* src, int n) {
 // Node i of a level has the children A i .. A i + A - 1 of the level below; the last child
 // CTA to arrive (one arrival counter per node) merges all of them and carries the result
 // up.  Returns true in exactly one CTA (the root owner), with the final triangle in Ra
-// (shared, ld NC).  `arena` holds Ra followed by room for A - 1 more triangles.  Slots of
+// (shared, ld NC).  `arena` holds Ra followed by room for A - 1 more triangles (A at most
+// tree_arity<NC>(), which sizes it).  Slots of
 // level l start at sum_{l' < l} width_l'; counters at sum_{l' < l} width_{l' + 1}.
-template <int NC, int T, int A>
-QL_DEV bool climb_tree(const TreeView& tv, int leaf, int n, double* arena, double* sd, int* s_flag) {
+template <int NC, int T>
+QL_DEV bool climb_tree(const TreeView& tv, int leaf, int n, double* arena, double* sd, int* s_flag, int A) {
   double* Ra = arena;
   double* Rbs = arena + NC * NC;
   __syncthreads();  // the leaf slot was written by all threads of this CTA

@@ -19,6 +19,7 @@ struct TsqrArgs {
   TreeView tv;
   int64_t tiles;
   int gated;  // FP64 fallback launch: run only if the range flag is set
+  int arity;  // R-tree arity (2 .. the column class's default)
   int epilogue;
   double* R;
   int64_t ldr;
@@ -54,7 +55,7 @@ __global__ void __launch_bounds__(T, 1) tsqr_kernel(TsqrArgs<S> a) {
     __stcg(slot + i, r <= c ? Ar::r_to_double(cta.R[r * NC + c]) : 0.0);
   }
   double* Ra = cta.arena;
-  if (!climb_tree<NC, T, tree_arity<NC>()>(a.tv, bid, n, cta.arena, cta.sd, &cta.misc[1])) return;
+  if (!climb_tree<NC, T>(a.tv, bid, n, cta.arena, cta.sd, &cta.misc[1], a.arity)) return;
 
   // root: every CTA has passed its range check and its tree arrival by now
   __threadfence();
@@ -104,6 +105,7 @@ ql_status launch_one(const TsqrCall& c, const TreeView& tv_in, int gated) {
   a.tv.leaves = (int)g;
   a.tiles = tiles;
   a.gated = gated;
+  a.arity = (c.arity >= 2 && c.arity < tree_arity<NC>()) ? c.arity : tree_arity<NC>();
   a.epilogue = c.epilogue;
   a.R = c.R;
   a.ldr = c.ldr;
@@ -127,7 +129,7 @@ template <typename S, typename Ar>
 ql_status dispatch(const TsqrCall& c, const TreeView& tv, int gated) {
   const int n = c.n;
   if constexpr (std::is_same<S, double>::value && std::is_same<Ar, ArithDF>::value) {
-    const int v = tsqr_variant();  // alternative thread layouts (tuning experiments)
+    const int v = c.variant >= 0 ? c.variant : tsqr_variant();  // alternative thread layouts (tuner)
     if (v > 0 && n > 8) {
       if (n <= 16) {
         if (v == 1) return launch_one<16, 4, 8, 256, S, Ar>(c, tv, gated);

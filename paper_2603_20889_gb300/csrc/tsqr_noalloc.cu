@@ -72,7 +72,12 @@ extern "C" ql_status ql_tsqr_qless_noalloc(int64_t m, int64_t n, const void* X, 
   c.ws_bytes = kNoAllocScratchBytes;
   c.stream = (cudaStream_t)stream;
   int ctas = 0;  // the autotuned grid, as the regular entry point uses (a table lookup, no allocation)
-  if (tune_lookup(m, n, dtype, 1.0, nullptr, &ctas)) c.ctas_per_sm = ctas;
+  int var = -1, ar = 0;
+  if (tune_lookup(m, n, dtype, 1.0, nullptr, &ctas, &var, &ar)) {
+    c.ctas_per_sm = ctas;
+    c.variant = var;
+    c.arity = ar;
+  }
   // tsqr_launch clears the counters and flags of the scratch on the stream before the
   // kernels run; the triangle slots are fully written before they are read.
   return tsqr_launch(c, current_arith());

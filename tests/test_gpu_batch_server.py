@@ -255,3 +255,97 @@ def test_server_cancel_withdraws_queued_requests_only():
     st = srv.stats()
     assert st.completed == 1 + len(rest) - len(cancelled)
     srv.close()
+
+
+def _method_test_instances(seed):
+    """Uneven problems of every tensor-core Gram class (9..64 columns) and narrower ones."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k, n in enumerate([3, 9, 16, 17, 24, 31, 32, 40, 48, 64, 12, 28]):
+        m = int(rng.integers(3000, 70000))
+        kind = 1 if k % 4 == 3 else 0
+        n = min(n, 63) if kind else n
+        kappa = float(10 ** rng.uniform(0, 5))
+        dt = np.float32 if k % 5 == 2 else np.float64
+        X = synth.conditioned(m, n, kappa, seed=seed * 100 + k).astype(dt)
+        b = (synth.gaussian(m, 1, seed=seed * 100 + k + 7)[:, 0]).astype(dt) if kind else None
+        out.append(dict(m=m, n=n, kind=kind, kappa=kappa, X=X, b=b, dt=dt))
+    return out
+
+
+@pytest.mark.parametrize("hint", ["cholqr2", "auto"])
+def test_batch_gram_method_class(hint):
+    """Cholesky-QR2 problems of a batch run as work items of the grouped tensor-core Gram
+    launches; every R (or least-squares solution) matches the oracle, and the plan reports
+    the method it chose per problem."""
+    import paper_2603_20889_gb300 as q
+
+    insts = _method_test_instances(7)
+    probs, keep = _problems(insts, q)
+    for p, it in zip(probs, insts):
+        p.method_hint = q.QL_CHOLQR2 if hint == "cholqr2" else q.QL_AUTO
+        p.kappa_hint = it["kappa"]
+    ws = q.batch_qless(probs)
+    torch.cuda.synchronize()
+    _check_outputs(insts, keep)
+    meth = (ctypes.c_int32 * len(probs))()
+    assert q.load_library().ql_batch_methods(ws.data_ptr(), meth, len(probs)) == q.QL_OK
+    for it, mth in zip(insts, meth):
+        ncols = it["n"] + it["kind"]
+        if ncols <= 8:
+            assert mth == q.QL_TSQR
+        elif hint == "cholqr2":
+            assert mth == q.QL_CHOLQR2
+        else:
+            assert mth == (q.QL_CHOLQR2 if ncols >= 24 else q.QL_TSQR)
+
+
+def test_batch_gram_problems_fall_back_to_tsqr():
+    """A Gram problem outside the double-float range, and (method chosen automatically) a
+    rank-deficient one whose Cholesky breaks down, are redone by the batch's FP64 TSQR
+    launch: both end with a valid R and info = QL_OK."""
+    import paper_2603_20889_gb300 as q
+
+    X1 = synth.conditioned(20000, 20, 1e2, seed=3) * 2.0 ** 70  # beyond the double-float range
+    x = synth.gaussian(30000, 25, seed=4)
+    X2 = np.column_stack([x, np.zeros(30000)])  # 26 columns, rank 25: the last pivot is exactly 0
+    insts = [dict(m=20000, n=20, kind=0, kappa=1e2, X=X1, b=None, dt=np.float64),
+             dict(m=30000, n=26, kind=0, kappa=1e3, X=X2, b=None, dt=np.float64)]
+    probs, keep = _problems(insts, q)
+    probs[0].method_hint, probs[0].kappa_hint = q.QL_CHOLQR2, 1e2
+    probs[1].method_hint, probs[1].kappa_hint = q.QL_AUTO, 1e3
+    ws = q.batch_qless(probs)
+    torch.cuda.synchronize()
+    (_, _, Ra, _, ia), (_, _, Rb, _, ib) = keep
+    assert info_of(ia) == [0, 0] and info_of(ib) == [0, 0]
+    Ra = to_host(Ra).reshape(-1).reshape((20, 20), order="F")
+    assert oracle.rel_err(Ra, oracle.householder_r(X1)) <= oracle.tolerance(20, 1e2)
+    Rb = to_host(Rb).reshape(-1).reshape((26, 26), order="F")
+    assert np.linalg.norm(Rb.T @ Rb - X2.T @ X2) <= 1e-12 * np.linalg.norm(X2) ** 2
+
+
+def test_batch_gram_class_replays_in_a_cuda_graph():
+    import paper_2603_20889_gb300 as q
+
+    insts = _method_test_instances(8)[:6]
+    probs, keep = _problems(insts, q)
+    for p, it in zip(probs, insts):
+        p.method_hint, p.kappa_hint = q.QL_CHOLQR2, it["kappa"]
+    L = q.load_library()
+    arr = (q.Problem * len(probs))(*probs)
+    nb = L.ql_batch_workspace_bytes(len(probs), arr)
+    ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        assert L.ql_batch_prepare(len(probs), arr, ws.data_ptr(), nb, q._stream_ptr(s)) == 0
+        assert L.ql_batch_launch(ws.data_ptr(), q._stream_ptr(s)) == 0  # first launch before capture
+    s.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        assert L.ql_batch_launch(ws.data_ptr(), q._stream_ptr(s)) == 0
+    for (_, _, R, _, info) in keep:
+        R.fill_(float("nan"))
+        info.fill_(-1)
+    g.replay()
+    torch.cuda.synchronize()
+    _check_outputs(insts, keep)
