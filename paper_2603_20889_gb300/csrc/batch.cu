@@ -128,10 +128,12 @@ QL_DEV void batch_chunk(const BatchItem& it, int64_t chunk, unsigned char* smem,
   if (!climb_tree<NC, T>(tv, (int)chunk, n, cta.arena, cta.sd, &cta.misc[1], tree_arity<NC>())) return;
   __threadfence();
   if (Ar::kRangeChecked && *(volatile int*)&flags[it.flag_idx] != 0) return;
+  // a Gram pass whose bounded wait gave up put the place into bits 8.. of the redo flag
+  const int tmo = Ar::kRangeChecked ? 0 : (*(volatile int*)&flags[it.flag_idx] >> 8) & 0xff;
   if (it.kind == 0)
-    epilogue_r<T>(Ra, NC, n, it.R, n, it.info, &cta.misc[2]);
+    epilogue_r<T>(Ra, NC, n, it.R, n, it.info, &cta.misc[2], tmo);
   else
-    epilogue_lstsq<T>(Ra, NC, n, it.x, it.x + (n - 1), it.R, it.info, cta.sd, &cta.misc[2]);
+    epilogue_lstsq<T>(Ra, NC, n, it.x, it.x + (n - 1), it.R, it.info, cta.sd, &cta.misc[2], tmo);
   __syncthreads();
 }
 

@@ -61,18 +61,17 @@ __global__ void __launch_bounds__(umma_threads<XF>(), 1)
   int64_t* s_work = reinterpret_cast<int64_t*>(smem_umma + (Sm::kBytes + 15) / 16 * 16);
   int* s_item = reinterpret_cast<int*>(s_work + 1);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(s_item + 1);
-  // tensor memory once per CTA: a CTA gives up its allocation permit after its first alloc
-  if ((threadIdx.x >> 5) == 0) tmem_alloc(tslot, Sh::TCOLS);
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tbase = *tslot;
+  // tensor memory and the barriers once per CTA: a CTA gives up its allocation permit after
+  // its first alloc, and a used barrier is not initialised again
+  const uint32_t tbase = umma_cta_begin<NC, S>(smem_umma, tslot);
+  UmmaBars bars;
   int64_t w;
   int idx;
-  while (claim(counter, items, count, total, s_work, s_item, w, idx)) {
+  // a CTA whose bounded wait gave up takes no more work (the others drain the list)
+  while (bars.ok && claim(counter, items, count, total, s_work, s_item, w, idx)) {
     GramArgs<S> a = *reinterpret_cast<const GramArgs<S>*>(&items[idx].args);
     a.pass = pass;
-    gram_umma_body<NC, S, XF>(a, (int)(w - items[idx].work_begin), items[idx].nchunks, tbase);
+    gram_umma_body<NC, S, XF>(a, (int)(w - items[idx].work_begin), items[idx].nchunks, tbase, bars);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();

@@ -62,8 +62,10 @@ struct GramArgs {
   int redo_on_breakdown;
 };
 
-QL_DEV void gram_request_redo(int* redo, int* redo_any) {
-  atomicOr(redo, 1);
+// Ask the batched FP64 TSQR launch to redo this problem.  Bits 8.. of the flag carry where a
+// bounded wait gave up (0: none), which that launch reports as {QL_ERR_TIMEOUT, where}.
+QL_DEV void gram_request_redo(int* redo, int* redo_any, int timeout_where = 0) {
+  atomicOr(redo, 1 | (timeout_where << 8));
   atomicOr(redo_any, 1);
 }
 
@@ -322,7 +324,7 @@ QL_DEV void gram_finish(const GramArgs<S>& a, unsigned char* smem, const int* co
   if (!misc[0]) return;
   __threadfence();
   if (Ar::kRangeChecked && *(volatile int*)&a.w.flags[0] != 0) {  // the FP64 launches redo it
-    if (a.redo && tid == 0) gram_request_redo(a.redo, a.redo_any);
+    if (a.redo && tid == 0) gram_request_redo(a.redo, a.redo_any, *(volatile int*)&a.w.flags[4]);
     return;
   }
 
@@ -1132,10 +1134,34 @@ __host__ __device__ constexpr int umma_threads() {
   return XF == kXNone ? 512 : 256;
 }
 
+// Phase parities of the two barriers of a tcgen05 Gram CTA, carried from one work item to
+// the next; ok turns false (uniformly across the CTA) once a bounded wait gave up.
+struct UmmaBars {
+  uint32_t phase = 0;   // MMA-completion barrier
+  uint32_t lphase = 0;  // tile (bulk copy) barrier
+  bool ok = true;
+};
+
+// Per-CTA set-up of the tcgen05 Gram kernels: the tensor-memory columns (written to *tslot
+// and returned) and the two barriers at UmmaSmem::kOffBar, each initialised once.
+template <int NC, typename S>
+QL_DEV uint32_t umma_cta_begin(unsigned char* smem, uint32_t* tslot) {
+  using Sm = UmmaSmem<NC, S>;
+  if ((threadIdx.x >> 5) == 0) tmem_alloc(tslot, UmmaShape<NC>::TCOLS);
+  if (threadIdx.x == 0) {
+    mbar_init(reinterpret_cast<uint64_t*>(smem + Sm::kOffBar), 1);
+    mbar_init(reinterpret_cast<uint64_t*>(smem + Sm::kOffBar + 8), 1);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  return *tslot;
+}
+
 // The body handles partial `bid` of `k` of one problem (see gram_tc_body) with the 512
-// tensor-memory columns at tbase that its caller allocated.
+// tensor-memory columns at tbase and the barriers that its caller set up (umma_cta_begin).
 template <int NC, typename S, int XF>
-QL_DEV void gram_umma_body(const GramArgs<S>& a, int bid, int k, uint32_t tbase) {
+QL_DEV void gram_umma_body(const GramArgs<S>& a, int bid, int k, uint32_t tbase, UmmaBars& bars) {
   using Sh = UmmaShape<NC>;
   using Sm = UmmaSmem<NC, S>;
   constexpr int T = umma_threads<XF>(), NW = T / 32, KT = Sh::KT, LDS = Sm::LDS, LDY = Sm::LDY, SP = Sh::SP,
@@ -1230,11 +1256,12 @@ QL_DEV void gram_umma_body(const GramArgs<S>& a, int bid, int k, uint32_t tbase)
     }
   }
 
-  // ---- the MMA-completion and tile barriers (the 7 accumulator blocks live at tbase)
-  if (tid == 0) {
-    mbar_init(mbar, 1);
-    mbar_init(lbar, 1);
-  }
+  // ---- the MMA-completion and tile barriers (the 7 accumulator blocks live at tbase) were
+  // initialised once by the kernel (umma_cta_begin): a persistent launch runs this body for
+  // many work items, and a barrier that copies and MMA commits have completed phases on is
+  // not initialised again; bars carries the parities.  The fence orders the previous item's
+  // generic shared-memory writes (its reduction and epilogue) before this item's bulk copies.
+  fence_proxy_async_smem();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -1275,7 +1302,7 @@ QL_DEV void gram_umma_body(const GramArgs<S>& a, int bid, int k, uint32_t tbase)
     }
     cp_async_commit();
   };
-  uint32_t lphase = 0;
+  uint32_t& lphase = bars.lphase;
   auto wait_tile = [&](int64_t t) -> bool {  // this thread's view: the staged tile t has landed
     if (!tile_bulk(t)) {
       cp_async_wait_all();
@@ -1317,7 +1344,7 @@ QL_DEV void gram_umma_body(const GramArgs<S>& a, int bid, int k, uint32_t tbase)
   int fail_where = 0;  // 1: a tile copy never completed, 2: the MMAs never completed
   if (t0 < t1) issue(t0);
   __syncthreads();
-  uint32_t phase = 0;
+  uint32_t& phase = bars.phase;
   for (int64_t t = t0; t < t1; ++t) {
     if (!__syncthreads_and(wait_tile(t))) {  // the copy engine did not deliver: FP64 redoes the call
       ok = false;
@@ -1512,9 +1539,12 @@ QL_DEV void gram_umma_body(const GramArgs<S>& a, int bid, int k, uint32_t tbase)
   cp_async_wait_all();  // an early exit may leave a prefetch in flight
   tc_fence_before();
   __syncthreads();
-  if (!ok && tid == 0) {  // the FP64 launches redo the call and report {QL_ERR_TIMEOUT, where}
-    atomicCAS(&a.w.flags[4], 0, fail_where);
-    atomicOr(&a.w.flags[0], 2);
+  if (!ok) {  // the FP64 launches redo the call and report {QL_ERR_TIMEOUT, where}
+    bars.ok = false;  // a late arrival may still complete a phase: the CTA takes no more work
+    if (tid == 0) {
+      atomicCAS(&a.w.flags[4], 0, fail_where);
+      atomicOr(&a.w.flags[0], 2);
+    }
   }
   if constexpr (XF == kXNone) {  // column exponents of the whole matrix, for the second pass
     for (int c = tid; c < n; c += T)
@@ -1544,12 +1574,9 @@ __global__ void __launch_bounds__(umma_threads<XF>(), 1) gram_umma_kernel(GramAr
   extern __shared__ __align__(1024) unsigned char smem_umma[];
   unsigned char* smem = smem_umma;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + Sm::kOffBar + 16);
-  if ((threadIdx.x >> 5) == 0) tmem_alloc(tslot, Sh::TCOLS);
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tbase = *tslot;
-  gram_umma_body<NC, S, XF>(a, blockIdx.x, gridDim.x, tbase);
+  const uint32_t tbase = umma_cta_begin<NC, S>(smem, tslot);
+  UmmaBars bars;
+  gram_umma_body<NC, S, XF>(a, blockIdx.x, gridDim.x, tbase, bars);
   tc_fence_before();
   __syncthreads();
   if ((threadIdx.x >> 5) == 0) tmem_dealloc(tbase, Sh::TCOLS);

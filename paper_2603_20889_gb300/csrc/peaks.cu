@@ -75,6 +75,33 @@ __global__ void __launch_bounds__(kPeakThreads) peak_df_kernel(float* out, int i
   out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+// Packed FP32 FMA (fma.rn.f32x2: two lanes per instruction, sm_100 and later).
+__global__ void __launch_bounds__(kPeakThreads) peak_fp32x2_kernel(float* out, int iters, float xs, float ys) {
+  unsigned long long a[8], x, y;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(x) : "f"(xs), "f"(xs));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(y) : "f"(ys), "f"(ys));
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const float t = (float)(threadIdx.x + k);
+    asm("mov.b64 %0, {%1, %2};" : "=l"(a[k]) : "f"(t), "f"(t));
+  }
+#pragma unroll 1
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int r = 0; r < 16; ++r)
+#pragma unroll
+      for (int k = 0; k < 8; ++k) asm volatile("fma.rn.f32x2 %0, %0, %1, %2;" : "+l"(a[k]) : "l"(x), "l"(y));
+  }
+  float s = 0.0f;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    float lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a[k]));
+    s += lo + hi;
+  }
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 // FP64 tensor-core MMA (mma.sync m8n8k4, 512 flops per warp instruction), 4 independent
 // accumulator tiles per warp.
 __global__ void __launch_bounds__(kPeakThreads) peak_dmma_kernel(double* out, int iters) {
@@ -134,8 +161,10 @@ extern "C" ql_status ql_measure_peaks(double* out, void* stream_) {
                    512.0 / 32 * 8 * 4, 500);
     out[3] = timed([&](int it) { peak_df_kernel<<<grid, kPeakThreads, 0, stream>>>((float*)buf, it, 0.999f, 1e-9f); },
                    2.0 * 4 * 8, 20000);
+    out[4] = timed([&](int it) { peak_fp32x2_kernel<<<grid, kPeakThreads, 0, stream>>>((float*)buf, it, 0.999f, 1e-3f); },
+                   2.0 * 2 * 16 * 8, 40000);
     if (cudaGetLastError() != cudaSuccess) st = QL_ERR_CUDA;
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 5; ++i)
       if (!(out[i] > 0.0)) st = QL_ERR_CUDA;
   }
   if (e0) cudaEventDestroy(e0);

@@ -349,3 +349,41 @@ def test_batch_gram_class_replays_in_a_cuda_graph():
     g.replay()
     torch.cuda.synchronize()
     _check_outputs(insts, keep)
+
+
+def test_batch_tcgen05_class_runs_many_items_per_cta():
+    """More (problem, chunk) work items of the 64-column class than SMs, so every CTA of the
+    persistent tcgen05 launches runs several items on the same barriers and tensor memory.
+    No bounded wait gives up (the FP64 redo would report {QL_ERR_TIMEOUT, where} in info),
+    and every R and least-squares solution matches the oracle."""
+    import time
+
+    import paper_2603_20889_gb300 as q
+
+    insts = []
+    for k in range(12):
+        kind = 1 if k % 6 == 5 else 0
+        n = (40, 48, 64)[k % 3] - kind
+        m = (1 << 17) + 37 * k  # ragged last tiles
+        dt = np.float32 if k % 4 == 1 else np.float64
+        kappa = 10.0 ** (1 + k % 4)
+        X = synth.conditioned(m, n, kappa, seed=900 + k).astype(dt)
+        b = (synth.gaussian(m, 1, seed=950 + k)[:, 0]).astype(dt) if kind else None
+        insts.append(dict(m=m, n=n, kind=kind, kappa=kappa, X=X, b=b, dt=dt))
+    probs, keep = _problems(insts, q)
+    for p, it in zip(probs, insts):
+        p.method_hint, p.kappa_hint = q.QL_CHOLQR2, it["kappa"]
+    q.batch_qless(probs)  # first call: plan, upload, module load
+    torch.cuda.synchronize()
+    for (_, _, R, _, info) in keep:
+        R.fill_(float("nan"))
+        info.fill_(-1)
+    t = time.perf_counter()
+    ws = q.batch_qless(probs)
+    torch.cuda.synchronize()
+    elapsed = time.perf_counter() - t
+    _check_outputs(insts, keep)
+    meth = (ctypes.c_int32 * len(probs))()
+    assert q.load_library().ql_batch_methods(ws.data_ptr(), meth, len(probs)) == q.QL_OK
+    assert list(meth) == [q.QL_CHOLQR2] * len(probs)
+    assert elapsed < 1.0, elapsed  # a bounded wait that gives up costs about 2 s
