@@ -84,10 +84,11 @@ uint64_t ql_launch_count(void);
 
 /*
  * Measured compute-pipe throughput of the current device (measurement support for the
- * roofline of the arithmetic-bound kernels; the paper has no counterpart).  Fills out[4]
+ * roofline of the arithmetic-bound kernels; the paper has no counterpart).  Fills out[5]
  * (host memory) with TFLOP/s: [0] FP32 FMA, [1] FP64 FMA, [2] FP64 tensor-core MMA
  * (mma.sync m8n8k4), [3] the library's double-float multiply-accumulate in FP64-equivalent
- * flops (2 per operation).  Synchronous: launches four timed kernels (a few tens of ms
+ * flops (2 per operation), [4] packed FP32 FMA (fma.rn.f32x2, two lanes per instruction).
+ * Synchronous: launches five timed kernels (a few tens of ms
  * each) on `stream`, allocates and frees one small device buffer.  QL_ERR_ARG for a null
  * out, QL_ERR_CUDA if a launch or the timing fails.
  */

@@ -170,10 +170,10 @@ def _colmajor(X):
 
 def measure_peaks(stream=None) -> dict:
     """Measured compute throughput of the current GPU in TFLOP/s (ql_measure_peaks)."""
-    out = (ctypes.c_double * 4)()
+    out = (ctypes.c_double * 5)()
     _check(load_library().ql_measure_peaks(ctypes.cast(out, ctypes.c_void_p), _stream_ptr(stream)),
            "ql_measure_peaks")
-    return {"fp32_fma": out[0], "fp64_fma": out[1], "fp64_mma": out[2], "df_fma": out[3]}
+    return {"fp32_fma": out[0], "fp64_fma": out[1], "fp64_mma": out[2], "df_fma": out[3], "fp32x2_fma": out[4]}
 
 
 def set_arith(mode: int) -> int:
