@@ -1,6 +1,7 @@
 // Grouped Gram passes of the batched form: the Cholesky-QR2 problems of a batch with at
-// least 9 columns run on the tensor-core Gram kernels (gram_tc_body for column classes 16
-// and 32, gram_umma_body for 64), one persistent launch per (column class, storage, pass).
+// least 9 columns run on the tensor-core Gram kernels (the first pass on gram_pipe_body;
+// the second on gram_tc_body for column classes 16 and 32, gram_umma_body for 64), one
+// persistent launch per (column class, storage, pass).
 // Every CTA claims (problem, chunk) work items from one atomic counter and runs the same
 // body as the single-call kernels on that chunk's row tiles, as partial `chunk` of the
 // problem's `nchunks`; the last chunk of a problem to finish runs its epilogue (the FP64
@@ -81,6 +82,31 @@ __global__ void __launch_bounds__(umma_threads<XF>(), 1)
   if ((threadIdx.x >> 5) == 0) tmem_dealloc(tbase, Sh::TCOLS);
 }
 
+template <int NC, typename S>
+__global__ void __launch_bounds__(PipeShape<NC>::T, 1)
+    gram_pipe_group_kernel(int* counter, const GramGroupItem* items, int count, int64_t total, int pass) {
+  using Sm = PipeSmem<NC, S>;
+  extern __shared__ __align__(1024) unsigned char smem_umma[];
+  int64_t* s_work = reinterpret_cast<int64_t*>(smem_umma + (Sm::kBytes + 15) / 16 * 16);
+  int* s_item = reinterpret_cast<int*>(s_work + 1);
+  // tensor memory and the barriers once per CTA (see gram_umma_group_kernel)
+  const uint32_t tbase = pipe_cta_begin<NC, S>(smem_umma);
+  PipeBars bars;
+  int64_t w;
+  int idx;
+  while (bars.ok && claim(counter, items, count, total, s_work, s_item, w, idx)) {
+    GramArgs<S> a = *reinterpret_cast<const GramArgs<S>*>(&items[idx].args);
+    a.pass = pass;
+    gram_pipe_body<NC, S>(a, (int)(w - items[idx].work_begin), items[idx].nchunks, tbase, bars);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+  }
+  tc_fence_before();
+  __syncthreads();
+  if ((threadIdx.x >> 5) == 0) tmem_dealloc(tbase, PipeShape<NC>::TCOLS);
+}
+
 template <typename K>
 static ql_status launch_group(K kern, int threads, size_t smem, int* counter, const GramGroupItem* items, int count,
                               int64_t total, int pass, cudaStream_t st) {
@@ -101,6 +127,11 @@ static ql_status launch_group(K kern, int threads, size_t smem, int* counter, co
 template <int NC, typename S>
 static ql_status launch_class(int* counter, const GramGroupItem* items, int count, int64_t total, int pass,
                               cudaStream_t st) {
+  if (pass == 1 && pipe_gram_enabled()) {
+    constexpr size_t smem = (PipeSmem<NC, S>::kBytes + 15) / 16 * 16 + 32;
+    return launch_group(gram_pipe_group_kernel<NC, S>, PipeShape<NC>::T, smem, counter, items, count, total, pass,
+                        st);
+  }
   if constexpr (NC == 64) {
     constexpr size_t smem = (UmmaSmem<NC, S>::kBytes + 15) / 16 * 16 + 32;
     if (pass == 1)

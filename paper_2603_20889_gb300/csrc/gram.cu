@@ -15,6 +15,14 @@ bool tc_gram_enabled() {
   return on;
 }
 
+bool pipe_gram_enabled() {
+  static const bool on = [] {
+    const char* v = std::getenv("QL_GRAM_PIPE");
+    return !(v && v[0] == '0');
+  }();
+  return on;
+}
+
 static int nc_of(int n) { return n <= 1 ? 1 : n <= 2 ? 2 : n <= 4 ? 4 : n <= 8 ? 8 : n <= 16 ? 16 : n <= 32 ? 32 : 64; }
 
 static size_t gram_layout(int n, GramWs* w, void* base) {
@@ -23,8 +31,8 @@ static size_t gram_layout(int n, GramWs* w, void* base) {
   const size_t keep = ((size_t)3 * nc * nc * sizeof(double) + 255) / 256 * 256;  // 3 n x n blocks (ld n)
   // one NC x NC partial per CTA (the streaming kernel for nc <= 4 runs up to 8 CTAs per SM)
   const size_t parts = (size_t)device_sm_count() * (nc <= 4 ? 8 : kGramMaxCtasPerSm) * nc * nc * sizeof(double);
-  // FP64 accumulators of the tcgen05 kernel (64 columns, one CTA per SM)
-  const size_t fbuf = nc == 64 ? (size_t)device_sm_count() * 64 * 128 * sizeof(double) : 0;
+  // FP64 accumulators of the tcgen05 kernels (16 to 64 columns, one CTA per SM)
+  const size_t fbuf = nc >= 16 ? (size_t)device_sm_count() * nc * 128 * sizeof(double) : 0;
   if (w && base) {
     unsigned char* b = static_cast<unsigned char*>(base);
     w->flags = reinterpret_cast<int*>(b);

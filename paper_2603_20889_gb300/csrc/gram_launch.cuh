@@ -10,6 +10,7 @@
 #include "small_dense.cuh"
 #include "gram_tc.cuh"
 #include "gram_umma.cuh"
+#include "gram_pipe.cuh"
 
 namespace ql {
 
@@ -1635,6 +1636,419 @@ ql_status gram_umma_launch_one(const GramCall& c, const GramWs& w, int pass) {
   return cudaPeekAtLastError() == cudaSuccess ? QL_OK : QL_ERR_CUDA;
 }
 
+// ---------------------------------------------------------------------------------------
+// Pipelined first Gram pass on tcgen05 (see gram_pipe.cuh).  The body handles the row tiles
+// [tiles bid / k, tiles (bid + 1) / k) of one problem as partial `bid` of `k`, with the
+// tensor memory at tbase and the barriers that pipe_cta_begin set up; bars carries their
+// phase counts from one work item to the next.
+template <int NC, int PLANE, int P = 0>
+QL_DEV void put_planes8(unsigned char* base, const long long (&Nb)[8]) {
+  uint4 w;
+  w.x = bf16x2_of_fields(digit_field8<P>(Nb[0]), digit_field8<P>(Nb[1]));
+  w.y = bf16x2_of_fields(digit_field8<P>(Nb[2]), digit_field8<P>(Nb[3]));
+  w.z = bf16x2_of_fields(digit_field8<P>(Nb[4]), digit_field8<P>(Nb[5]));
+  w.w = bf16x2_of_fields(digit_field8<P>(Nb[6]), digit_field8<P>(Nb[7]));
+  *reinterpret_cast<uint4*>(base + P * PLANE) = w;
+  if constexpr (P + 1 < 8) put_planes8<NC, PLANE, P + 1>(base, Nb);
+}
+
+template <typename S>
+QL_DEV void load8(S (&v)[8], const S* p);  // 8 consecutive staged elements (16-byte aligned)
+template <>
+QL_DEV void load8<double>(double (&v)[8], const double* p) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const double2 t = reinterpret_cast<const double2*>(p)[q];
+    v[2 * q] = t.x;
+    v[2 * q + 1] = t.y;
+  }
+}
+template <>
+QL_DEV void load8<float>(float (&v)[8], const float* p) {
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const float4 t = reinterpret_cast<const float4*>(p)[q];
+    v[4 * q] = t.x;
+    v[4 * q + 1] = t.y;
+    v[4 * q + 2] = t.z;
+    v[4 * q + 3] = t.w;
+  }
+}
+
+template <int NC, typename S>
+QL_DEV void gram_pipe_body(GramArgs<S> a, int bid, int k, uint32_t tbase, PipeBars& bars) {
+  using Sh = PipeShape<NC>;
+  using Sm = PipeSmem<NC, S>;
+  constexpr int T = Sh::T, TS = Sh::TS, UPT = Sh::UPT, KT = Sh::KT, LDS = Sm::LDS, SP = Sh::SP,
+                PLANE = Sh::PLANE, SBO = Sh::SBO, LBO = Sh::LBO, HALF = Sh::HALF, G = Sh::G;
+  constexpr uint32_t IDESC = umma_idesc_bf16(128, 128);
+  extern __shared__ __align__(1024) unsigned char smem_umma[];
+  unsigned char* smem = smem_umma;
+  const int tid = threadIdx.x, n = a.n, lane = tid & 31, warp = tid >> 5;
+  const bool control = warp == TS / 32;
+
+  unsigned char* dig0 = smem + Sm::kOffDig;
+  S* raw0 = reinterpret_cast<S*>(smem + Sm::kOffRaw);
+  float* pow2c = reinterpret_cast<float*>(smem + Sm::kOffPow);
+  int* scale = reinterpret_cast<int*>(smem + Sm::kOffScale);  // running scale exponents (biased)
+  int* colmax = reinterpret_cast<int*>(smem + Sm::kOffColmax);
+  int* misc = reinterpret_cast<int*>(smem + Sm::kOffMisc);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + Sm::kOffBar);  // [2] MMAs done, per digit buffer
+  uint64_t* lbar = mbar + 2;                                          // [2] tile landed, per raw stage
+  uint64_t* dbar = mbar + 4;                                          // [2] digits ready, per digit buffer
+  int* ngrp = reinterpret_cast<int*>(smem + Sm::kOffSlot + 4);        // [2] tile opens a new group
+  int* sfail = ngrp + 2;                                              // [2] where each role gave up
+
+  a.tiles = (a.m + KT - 1) / KT;  // in this kernel's tile height
+  for (int i = tid; i < NC; i += T) {
+    colmax[i] = 0;
+    scale[i] = 0;
+    pow2c[i] = 0.0f;
+  }
+  if (tid < 2) sfail[tid] = 0;
+  // the previous work item's generic writes (its reduction and epilogue) come before this
+  // item's bulk copies and MMA operand reads
+  fence_proxy_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+
+  const int64_t t0 = a.tiles * bid / k, t1 = a.tiles * (bid + 1) / k;
+  // a full tile of 16-byte aligned columns arrives by bulk copies; the slicers read any other
+  // tile (the ragged last one, or X not 16-byte aligned) from global memory themselves
+  auto tile_bulk = [&](int64_t t) { return a.bulk != 0 && (t + 1) * KT <= a.m; };
+
+  // this slicer's units of a tile: unit u = tid + TS uu covers rows r0..r0+7 of column c
+  // (8 consecutive threads hold 8 consecutive columns, so their digit stores fill whole
+  // core-matrix rows)
+  int c_[UPT], r0_[UPT];
+  bool live_[UPT];
+#pragma unroll
+  for (int uu = 0; uu < UPT; ++uu) {
+    const int u = (tid & (TS - 1)) + TS * uu, u8 = u >> 3, rg = u8 % (KT / 8), cg = u8 / (KT / 8);
+    c_[uu] = 8 * cg + (u & 7);
+    r0_[uu] = 8 * rg;
+    live_[uu] = c_[uu] < n && !control;
+  }
+  // read-out role: TMEM lane quarter qd, column part hh; lane L is plane offset kq, column li
+  const int qd = warp & 3, hh = (warp >> 2) % (TS / 128);
+  const int L = 32 * qd + lane, kq = L / NC, li = L % NC;
+  df acc[HALF];
+#pragma unroll
+  for (int j = 0; j < HALF; ++j) acc[j] = df{0.0f, 0.0f};
+  // FP64 level of the accumulators: this CTA's [NC columns][128 lanes] block of the
+  // workspace (L2-resident; each slicer touches only its own entries)
+  double* fb = a.w.fbuf + (size_t)bid * NC * 128;
+  int erun[UPT];  // largest exponent each unit's column has shown this slicer (range record)
+#pragma unroll
+  for (int uu = 0; uu < UPT; ++uu) erun[uu] = 0;
+
+  if (control) {
+    // ---- control warp: copies two tiles ahead, then per tile: wait for its digits, copy the
+    // tile two ahead into the stage they were cut from, issue the MMAs and commit them
+    bool ok = true;
+    uint32_t pend = 0u, ppar = 0u;  // bit b: a copy into stage b in flight, and its phase parity
+    auto copy = [&](int64_t t, int b) {
+      if (!tile_bulk(t)) return;
+      S* stage = raw0 + (size_t)b * NC * LDS;
+      const int64_t row0 = t * KT;
+      if (lane == 0) mbar_arrive_expect_tx(&lbar[b], (uint32_t)(n * KT * sizeof(S)));
+      __syncwarp();
+      for (int cc = lane; cc < n; cc += 32) bulk_g2s(stage + cc * LDS, a.src.col(cc) + row0, KT * sizeof(S), &lbar[b]);
+      pend |= 1u << b;
+      ppar = (ppar & ~(1u << b)) | (bars.lpar & (1u << b));
+      bars.lpar ^= 1u << b;
+    };
+    if (t0 < t1) copy(t0, 0);
+    if (t0 + 1 < t1) copy(t0 + 1, 1);
+    for (int64_t t = t0; t < t1; ++t) {
+      const int b = (int)((t - t0) & 1);
+      if (!__all_sync(0xffffffffu, mbar_wait_bounded(&dbar[b], (bars.mpar >> b) & 1u))) {
+        ok = false;
+        break;
+      }
+      bars.mpar ^= 1u << b;
+      pend &= ~(1u << b);  // the slicers have read stage b
+      tc_fence_after();
+      if (t + 2 < t1) copy(t + 2, b);
+      if (lane == 0) {
+        const uint32_t fresh = (uint32_t)ngrp[b];
+        // descriptor of plane 0, k-step 0; other planes and k-steps add (byte offset >> 4)
+        // to the 14-bit address field, which stays below 2^14 (shared addresses < 256 KB)
+        const uint64_t d0 = umma_sdesc(smem_addr(dig0 + (size_t)b * Sh::DBUF), LBO, SBO);
+#pragma unroll 1
+        for (int kk = 0; kk < KT / 16; ++kk) {
+          const uint64_t dk = d0 + (uint64_t)((kk * 2 * LBO) >> 4);
+#pragma unroll
+          for (int p0 = 0; p0 < 8; p0 += SP)
+#pragma unroll
+            for (int q0 = 0; q0 < 8; q0 += SP)
+              if (p0 + q0 <= 7)
+                umma_bf16(tbase + (uint32_t)((p0 + q0) * NC), dk + (uint64_t)((p0 * PLANE) >> 4),
+                          dk + (uint64_t)((q0 * PLANE) >> 4), IDESC, (!fresh || kk > 0 || p0 > 0) ? 1u : 0u);
+        }
+        umma_commit(&mbar[b]);
+      }
+      __syncwarp();
+    }
+    // no copy may still be writing when the CTA moves on
+    for (int b = 0; b < 2; ++b)
+      if (pend & (1u << b)) mbar_wait_bounded(&lbar[b], (ppar >> b) & 1u);
+    if (!ok && lane == 0) sfail[1] = 2;
+  } else {
+    // ---- slicer warps
+    bool ok = true;
+    int fail_where = 0;   // 1: a tile copy never completed, 2: the MMAs never completed
+    int grp = 0;          // tiles summed in tensor memory since the last read-out
+    int nread = 0;        // read-outs since the last move into FP64
+    int last_b = 0;       // digit buffer of the latest tile handed to the MMAs
+    uint32_t cpar = 0u;   // bit b: phase parity of the MMAs of the latest tile on buffer b
+#pragma unroll
+    for (int j = 0; j < HALF; ++j) __stcg(fb + (size_t)(hh * HALF + j) * 128 + L, 0.0);
+
+    // fold the eight accumulator combinations into the double-float sums: combination tb of
+    // this lane sits at column tb NC + j and weighs tb + kq (above 7: beyond the truncation,
+    // masked).  Every block value is an exact integer and every product with its
+    // power-of-two weight is exact; the weights are summed with exact two-sums.
+    auto readout = [&]() {
+      const float fi = pow2c[li];
+      float sw[8];
+      uint32_t vm[8];
+#pragma unroll
+      for (int tb = 0; tb < 8; ++tb) {
+        const int w = tb + kq;
+        sw[tb] = w <= 7 ? fi * __int_as_float((127 - kDigitScaleLog2 - 7 * w) << 23) : 0.0f;
+        vm[tb] = w <= 7 ? 0xffffffffu : 0u;
+      }
+      const uint32_t lane_base = tbase + ((uint32_t)(32 * qd) << 16) + (uint32_t)(hh * HALF);
+#pragma unroll
+      for (int c0 = 0; c0 < HALF; c0 += 4) {
+        uint32_t v[8][4];
+#pragma unroll
+        for (int tb = 0; tb < 8; ++tb) tmem_ld(lane_base + (uint32_t)(tb * NC + c0), v[tb]);
+        tmem_ld_wait();
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          float hi = __uint_as_float(v[7][j] & vm[7]) * sw[7], lo = 0.0f;
+#pragma unroll
+          for (int tb = 6; tb >= 0; --tb) {
+            float s2, e2;
+            two_sum(hi, __uint_as_float(v[tb][j] & vm[tb]) * sw[tb], s2, e2);
+            hi = s2;
+            lo = __fadd_rn(lo, e2);
+          }
+          const float fj = pow2c[hh * HALF + c0 + j];
+          acc[c0 + j] = df_add(acc[c0 + j], df{hi * fj, lo * fj});
+        }
+      }
+    };
+
+    for (int64_t t = t0; t < t1; ++t) {
+      const int i = (int)(t - t0), b = i & 1;
+      unsigned char* dig = dig0 + (size_t)b * Sh::DBUF;
+      const bool bulk = tile_bulk(t);
+      bool landed = true;
+      if (bulk) {
+        landed = mbar_wait_bounded(&lbar[b], (bars.lpar >> b) & 1u);
+        bars.lpar ^= 1u << b;
+      }
+      if (!slicer_and<TS>(landed)) {  // the copy engine did not deliver: FP64 redoes the call
+        ok = false;
+        fail_where = 1;
+        break;
+      }
+      S v[UPT][8];
+      int e[UPT];
+      bool over = false;
+#pragma unroll
+      for (int uu = 0; uu < UPT; ++uu) {
+        e[uu] = 0;
+        if (live_[uu]) {
+          if (bulk) {
+            load8<S>(v[uu], raw0 + (size_t)b * NC * LDS + c_[uu] * LDS + r0_[uu]);
+          } else {
+            const S* col = a.src.col(c_[uu]);
+            const int64_t row0 = t * KT + r0_[uu];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v[uu][j] = row0 + j < a.m ? __ldg(col + row0 + j) : S(0);
+          }
+#pragma unroll
+          for (int j = 0; j < 8; ++j) e[uu] = max(e[uu], elem_exponent(v[uu][j]));
+          erun[uu] = max(erun[uu], e[uu]);
+          over = over || e[uu] > scale[c_[uu]];
+        } else {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) v[uu][j] = S(0);
+        }
+      }
+      // digit buffer b is free once the MMAs of tile t - 2 are done; a column whose tile
+      // maximum exceeds its scale, or a full group, needs a read-out first (rare)
+      const bool okw = i >= 2 ? mbar_wait_bounded(&mbar[b], (cpar >> b) & 1u) : true;
+      const bool full = grp >= G;
+      if (slicer_or<TS>(over || !okw) || full) {
+        if (!slicer_and<TS>(okw)) {  // the tensor core did not finish: FP64 redoes the call
+          ok = false;
+          fail_where = 2;
+          break;
+        }
+        const bool anyover = slicer_or<TS>(over);
+        if ((anyover || full) && grp > 0) {  // read the sums out before their scale changes or they could round
+          if (!slicer_and<TS>(mbar_wait_bounded(&mbar[last_b], (cpar >> last_b) & 1u))) {
+            ok = false;
+            fail_where = 2;
+            break;
+          }
+          tc_fence_after();
+          readout();
+          grp = 0;
+          if (++nread == Sh::DF_FLUSH) {  // double-float sums -> FP64 (L2)
+#pragma unroll
+            for (int j = 0; j < HALF; ++j) {
+              double* f = fb + (size_t)(hh * HALF + j) * 128 + L;
+              __stcg(f, __ldcg(f) + df_to_double(acc[j]));
+              acc[j] = df{0.0f, 0.0f};
+            }
+            nread = 0;
+          }
+          slicer_sync<TS>();  // every read of the blocks and of the old scales is done
+        }
+#pragma unroll
+        for (int uu = 0; uu < UPT; ++uu)
+          if (live_[uu] && e[uu] > scale[c_[uu]]) atomicMax(&scale[c_[uu]], e[uu] + Sh::SLACK);
+        slicer_sync<TS>();
+        for (int cc = tid; cc < NC; cc += TS) {
+          const int s = scale[cc];
+          pow2c[cc] = s > 0 ? __int_as_float(max(1, min(254, s - 895)) << 23) : 0.0f;  // 2^(s - 1022)
+        }
+      }
+      // eight digits of every element into the core-matrix layout of buffer b
+#pragma unroll
+      for (int uu = 0; uu < UPT; ++uu) {
+        const int cu = c_[uu], Es = live_[uu] ? scale[cu] : 0;
+        long long Nb[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) Nb[j] = (live_[uu] ? fixed56<S>(v[uu][j], Es) : 0ll) + kDigitBias8;
+        put_planes8<NC, PLANE>(dig + (cu >> 3) * SBO + (r0_[uu] >> 3) * LBO + (cu & 7) * 16, Nb);
+      }
+      if (tid == 0) ngrp[b] = grp == 0 ? 1 : 0;
+      fence_proxy_async_smem();  // the digit planes are read by the tensor core
+      tc_fence_before();         // the read-out's TMEM loads come before the next MMAs
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&dbar[b]);
+      cpar = (cpar & ~(1u << b)) | (bars.mpar & (1u << b));
+      bars.mpar ^= 1u << b;
+      last_b = b;
+      ++grp;
+    }
+    if (ok && grp > 0) {  // the last group
+      if (!slicer_and<TS>(mbar_wait_bounded(&mbar[last_b], (cpar >> last_b) & 1u))) {
+        ok = false;
+        fail_where = 2;
+      } else {
+        tc_fence_after();
+        readout();
+      }
+    }
+    if (!ok && tid == 0) sfail[0] = fail_where;
+#pragma unroll
+    for (int uu = 0; uu < UPT; ++uu)
+      if (live_[uu] && erun[uu] > 0) atomicMax(&colmax[c_[uu]], erun[uu]);
+  }
+  tc_fence_before();
+  __syncthreads();
+  const int fw = sfail[0] ? sfail[0] : sfail[1];
+  if (fw) {
+    bars.ok = false;  // a late arrival may still complete a phase: the CTA takes no more work
+    if (tid == 0) {   // the FP64 launches redo the call and report {QL_ERR_TIMEOUT, where}
+      atomicCAS(&a.w.flags[4], 0, fw);
+      atomicOr(&a.w.flags[0], 2);
+    }
+  }
+  for (int cc = tid; cc < n; cc += T)  // column exponents of the whole matrix, for the second pass
+    if (colmax[cc] > 0) atomicMax(&a.w.flags[64 + cc], colmax[cc]);
+  // combine the plane offsets of each entry (FP64) and store this CTA's partial Gram matrix
+  double* red = reinterpret_cast<double*>(smem + Sm::kOffDig);  // [lane L][column]
+  if (!control) {
+#pragma unroll
+    for (int j = 0; j < HALF; ++j)
+      red[L * NC + hh * HALF + j] = __ldcg(fb + (size_t)(hh * HALF + j) * 128 + L) + df_to_double(acc[j]);
+  }
+  __syncthreads();
+  double* part = a.w.partials + (size_t)bid * NC * NC;
+  for (int e2 = tid; e2 < NC * NC; e2 += T) {
+    const int i = e2 / NC, j = e2 % NC;
+    double s = 0.0;
+#pragma unroll
+    for (int kk = 0; kk < SP; ++kk) s += red[(kk * NC + i) * NC + j];
+    __stcg(part + e2, s);
+  }
+  gram_finish<NC, T, S, ArithDF>(a, smem, colmax, misc, k);
+}
+
+template <int NC, typename S>
+__global__ void __launch_bounds__(PipeShape<NC>::T, 1) gram_pipe_kernel(GramArgs<S> a) {
+  extern __shared__ __align__(1024) unsigned char smem_umma[];
+  const uint32_t tbase = pipe_cta_begin<NC, S>(smem_umma);
+  PipeBars bars;
+  gram_pipe_body<NC, S>(a, blockIdx.x, gridDim.x, tbase, bars);
+  tc_fence_before();
+  __syncthreads();
+  if ((threadIdx.x >> 5) == 0) tmem_dealloc(tbase, PipeShape<NC>::TCOLS);
+}
+
+template <int NC, typename S>
+ql_status gram_pipe_launch_one(const GramCall& c, const GramWs& w) {
+  using Sh = PipeShape<NC>;
+  using Sm = PipeSmem<NC, S>;
+  auto kern = gram_pipe_kernel<NC, S>;
+  static bool ready = false;
+  static std::mutex mu;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (!ready) {
+      if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sm::kBytes) != cudaSuccess)
+        return QL_ERR_CUDA;
+      ready = true;
+    }
+  }
+  // one CTA per SM: the shared memory allows no second one
+  const int64_t tiles = (c.m + Sh::KT - 1) / Sh::KT;
+  int64_t g = (int64_t)device_sm_count();
+  if (g > tiles) g = tiles;
+  if (g < 1) g = 1;
+  GramArgs<S> a{};
+  a.src.A = static_cast<const S*>(c.A);
+  a.src.lda = c.lda;
+  a.src.b = static_cast<const S*>(c.b);
+  a.src.nA = c.nA;
+  a.m = c.m;
+  a.n = c.n;
+  a.tiles = tiles;
+  a.pass = 1;
+  a.method = c.method;
+  a.gated = 0;
+  a.epilogue = c.epilogue;
+  a.w = w;
+  a.R = c.R;
+  a.ldr = c.ldr;
+  a.Z = c.Z;
+  a.rank_tol = c.rank_tol;
+  a.x = c.x;
+  a.resnorm = c.resnorm;
+  a.Rext = c.Rext;
+  a.info = c.info;
+  {
+    auto aligned = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+    bool b = aligned(c.A) && ((size_t)c.lda * sizeof(S)) % 16 == 0;
+    if (c.nA < c.n) b = b && aligned(c.b);
+    a.bulk = b ? 1 : 0;
+  }
+  a.mround = 2;
+  count_launch();
+  kern<<<(int)g, Sh::T, Sm::kBytes, c.stream>>>(a);
+  return cudaPeekAtLastError() == cudaSuccess ? QL_OK : QL_ERR_CUDA;
+}
+
 template <int NC, typename S, typename Ar, int XF>
 ql_status gram_launch_one(const GramCall& c, const GramWs& w, int pass, int gated) {
   using Sh = GramShape<NC>;
@@ -1692,17 +2106,20 @@ ql_status gram_dispatch(const GramCall& c, const GramWs& w, int gated) {
     constexpr int NC = decltype(nc_tag)::value;
     if constexpr (NC >= 16 && std::is_same<Ar, ArithDF>::value) {
       if (tc_gram_enabled()) {
-        // tcgen05 for 64 columns; below that, stacking 128 / NC planes would spread every
-        // weight over 4 or 8 lane groups and the TMEM read-out cost more than mma.sync saves
+        // first pass: the pipelined tcgen05 kernel (its read-outs are rare, so stacking
+        // 128 / NC planes costs little).  Later passes: tcgen05 per tile for 64 columns;
+        // below that mma.sync, whose per-tile read-out is cheaper than TMEM's
         if constexpr (NC == 64) {
-          ql_status st = gram_umma_launch_one<NC, S, kXNone>(c, w, 1);
+          ql_status st =
+              pipe_gram_enabled() ? gram_pipe_launch_one<NC, S>(c, w) : gram_umma_launch_one<NC, S, kXNone>(c, w, 1);
           if (st) return st;
           if (c.method == QL_SVQB2) return gram_umma_launch_one<NC, S, kXFull>(c, w, 2);
           st = gram_umma_launch_one<NC, S, kXUpper>(c, w, 2);
           if (st || c.method != QL_SCHOLQR3) return st;
           return gram_umma_launch_one<NC, S, kXUpper>(c, w, 3);
         } else {
-          ql_status st = gram_tc_launch_one<NC, S, kXNone>(c, w, 1);
+          ql_status st =
+              pipe_gram_enabled() ? gram_pipe_launch_one<NC, S>(c, w) : gram_tc_launch_one<NC, S, kXNone>(c, w, 1);
           if (st) return st;
           if (c.method == QL_SVQB2) return gram_tc_launch_one<NC, S, kXFull>(c, w, 2);
           st = gram_tc_launch_one<NC, S, kXUpper>(c, w, 2);

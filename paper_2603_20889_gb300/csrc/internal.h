@@ -84,6 +84,9 @@ ql_status check_r(const double* R, int64_t ldr, int64_t n);
 // Whether the Gram passes use the tensor-core kernels (double-float mode, n >= 9);
 // the environment variable QL_GRAM_SIMT=1 selects the SIMT kernels instead.
 bool tc_gram_enabled();
+// First Gram pass of the 16-, 32- and 64-column classes on the pipelined tcgen05 kernel
+// (default; QL_GRAM_PIPE=0 selects the per-tile kernels, for comparison).
+bool pipe_gram_enabled();
 
 // Thread-layout variant of the TSQR kernels (environment QL_TSQR_CFG, 0 = default).
 int tsqr_variant();
