@@ -341,7 +341,7 @@ static bool make_plan(int32_t count, const ql_problem* probs, BatchPlan& P, unsi
     GramArgs<double>& a = gi.args;
     const size_t keep_b = ((size_t)3 * nc * nc * sizeof(double) + 255) / 256 * 256;
     const size_t part_b = (size_t)nch * nc * nc * sizeof(double);
-    const size_t fbuf_b = (size_t)nch * nc * 128 * sizeof(double);  // FP64 level of the tcgen05 kernels
+    const size_t fbuf_b = (size_t)nch * nc * 128 * 2 * sizeof(double);  // accumulator levels of the tcgen05 kernels
     const size_t flags_off = P.off_gflags + (size_t)fb * 512, keep_off = off, part_off = off + keep_b,
                  fbuf_off = off + keep_b + part_b;
     off += keep_b + part_b + fbuf_b;
@@ -378,6 +378,9 @@ static bool make_plan(int32_t count, const ql_problem* probs, BatchPlan& P, unsi
       if (it.kind == 1) b = b && al16(it.b);
       a.bulk = b ? 1 : 0;
     }
+    gi.tma = pipe_tensor_maps(&gi.tmA, it.kind == 1 ? &gi.tmB : nullptr, it.A, it.b, it.dtype, it.m, it.nA, it.lda)
+                 ? 1
+                 : 0;
     a.mround = 2;
     a.redo = reinterpret_cast<int*>(at(P.off_flags)) + 1 + k;
     a.redo_any = reinterpret_cast<int*>(at(P.off_flags));

@@ -97,7 +97,9 @@ __global__ void __launch_bounds__(PipeShape<NC>::T, 1)
   while (bars.ok && claim(counter, items, count, total, s_work, s_item, w, idx)) {
     GramArgs<S> a = *reinterpret_cast<const GramArgs<S>*>(&items[idx].args);
     a.pass = pass;
-    gram_pipe_body<NC, S>(a, (int)(w - items[idx].work_begin), items[idx].nchunks, tbase, bars);
+    a.bulk = items[idx].tma;
+    gram_pipe_body<NC, S>(a, (int)(w - items[idx].work_begin), items[idx].nchunks, tbase, bars, &items[idx].tmA,
+                          items[idx].tma && a.src.nA < a.n ? &items[idx].tmB : nullptr);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();

@@ -6,12 +6,15 @@
 namespace ql {
 
 // One Gram-method problem of a grouped launch: its single-call arguments (float storage has
-// the same layout), the first work index of its chunks in the launch and their number.
+// the same layout), the first work index of its chunks in the launch and their number, and
+// the tensor maps of its columns for the pipelined first pass (see pipe_tensor_maps).
 struct GramGroupItem {
   GramArgs<double> args;
   int64_t work_begin;
   int nchunks;
-  int pad;
+  int tma;          // tmA (and tmB for least squares) are valid
+  CUtensorMap tmA;  // 64-byte aligned: the item array is uploaded as it is laid out here
+  CUtensorMap tmB;
 };
 
 // One persistent launch over `count` items (total work = their chunks) of column class nc

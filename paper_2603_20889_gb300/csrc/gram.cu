@@ -23,6 +23,46 @@ bool pipe_gram_enabled() {
   return on;
 }
 
+bool pipe_tensor_maps(CUtensorMap* tmA, CUtensorMap* tmB, const void* A, const void* b, int dtype, int64_t m, int nA,
+                      int64_t lda) {
+  using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  static const Encode encode = [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return (Encode) nullptr;
+    return reinterpret_cast<Encode>(fn);
+  }();
+  const size_t es = dtype == QL_F64 ? 8 : 4;
+  auto aligned = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+  if (!encode || m < 1 || m >= (int64_t(1) << 31) || nA < 1 || nA > 256 || !aligned(A) || ((size_t)lda * es) % 16 ||
+      (tmB && !aligned(b)))
+    return false;
+  const CUtensorMapDataType dt = dtype == QL_F64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  const cuuint32_t box_rows = (cuuint32_t)(128 / es), es1[2] = {1, 1};
+  {
+    const cuuint64_t dims[2] = {(cuuint64_t)m, (cuuint64_t)nA}, strides[1] = {(cuuint64_t)lda * es};
+    const cuuint32_t box[2] = {box_rows, (cuuint32_t)nA};
+    if (encode(tmA, dt, 2, const_cast<void*>(A), dims, strides, box, es1, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+        CUDA_SUCCESS)
+      return false;
+  }
+  if (tmB) {
+    const cuuint64_t dims[2] = {(cuuint64_t)m, 1}, strides[1] = {((cuuint64_t)m * es + 15) / 16 * 16};
+    const cuuint32_t box[2] = {box_rows, 1};
+    // unswizzled: its box lands at line kb NC + nA, 128-byte but not 1024-byte aligned
+    if (encode(tmB, dt, 2, const_cast<void*>(b), dims, strides, box, es1, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+        CUDA_SUCCESS)
+      return false;
+  }
+  return true;
+}
+
 static int nc_of(int n) { return n <= 1 ? 1 : n <= 2 ? 2 : n <= 4 ? 4 : n <= 8 ? 8 : n <= 16 ? 16 : n <= 32 ? 32 : 64; }
 
 static size_t gram_layout(int n, GramWs* w, void* base) {
@@ -31,8 +71,9 @@ static size_t gram_layout(int n, GramWs* w, void* base) {
   const size_t keep = ((size_t)3 * nc * nc * sizeof(double) + 255) / 256 * 256;  // 3 n x n blocks (ld n)
   // one NC x NC partial per CTA (the streaming kernel for nc <= 4 runs up to 8 CTAs per SM)
   const size_t parts = (size_t)device_sm_count() * (nc <= 4 ? 8 : kGramMaxCtasPerSm) * nc * nc * sizeof(double);
-  // FP64 accumulators of the tcgen05 kernels (16 to 64 columns, one CTA per SM)
-  const size_t fbuf = nc >= 16 ? (size_t)device_sm_count() * nc * 128 * sizeof(double) : 0;
+  // accumulators of the tcgen05 kernels (16 to 64 columns, one CTA per SM): an FP64 and a
+  // double-float level per CTA (the per-tile kernel of the later passes uses the first)
+  const size_t fbuf = nc >= 16 ? (size_t)device_sm_count() * nc * 128 * 2 * sizeof(double) : 0;
   if (w && base) {
     unsigned char* b = static_cast<unsigned char*>(base);
     w->flags = reinterpret_cast<int*>(b);

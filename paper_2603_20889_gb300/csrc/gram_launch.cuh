@@ -1642,45 +1642,23 @@ ql_status gram_umma_launch_one(const GramCall& c, const GramWs& w, int pass) {
 // tensor memory at tbase and the barriers that pipe_cta_begin set up; bars carries their
 // phase counts from one work item to the next.
 template <int NC, int PLANE, int P = 0>
-QL_DEV void put_planes8(unsigned char* base, const long long (&Nb)[8]) {
+QL_DEV void put_planes8(unsigned char* base, const unsigned long long (&Nb)[8]) {
   uint4 w;
-  w.x = bf16x2_of_fields(digit_field8<P>(Nb[0]), digit_field8<P>(Nb[1]));
-  w.y = bf16x2_of_fields(digit_field8<P>(Nb[2]), digit_field8<P>(Nb[3]));
-  w.z = bf16x2_of_fields(digit_field8<P>(Nb[4]), digit_field8<P>(Nb[5]));
-  w.w = bf16x2_of_fields(digit_field8<P>(Nb[6]), digit_field8<P>(Nb[7]));
+  w.x = digit_word<P>(Nb[0], Nb[1]);
+  w.y = digit_word<P>(Nb[2], Nb[3]);
+  w.z = digit_word<P>(Nb[4], Nb[5]);
+  w.w = digit_word<P>(Nb[6], Nb[7]);
   *reinterpret_cast<uint4*>(base + P * PLANE) = w;
   if constexpr (P + 1 < 8) put_planes8<NC, PLANE, P + 1>(base, Nb);
 }
 
-template <typename S>
-QL_DEV void load8(S (&v)[8], const S* p);  // 8 consecutive staged elements (16-byte aligned)
-template <>
-QL_DEV void load8<double>(double (&v)[8], const double* p) {
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const double2 t = reinterpret_cast<const double2*>(p)[q];
-    v[2 * q] = t.x;
-    v[2 * q + 1] = t.y;
-  }
-}
-template <>
-QL_DEV void load8<float>(float (&v)[8], const float* p) {
-#pragma unroll
-  for (int q = 0; q < 2; ++q) {
-    const float4 t = reinterpret_cast<const float4*>(p)[q];
-    v[4 * q] = t.x;
-    v[4 * q + 1] = t.y;
-    v[4 * q + 2] = t.z;
-    v[4 * q + 3] = t.w;
-  }
-}
-
 template <int NC, typename S>
-QL_DEV void gram_pipe_body(GramArgs<S> a, int bid, int k, uint32_t tbase, PipeBars& bars) {
+QL_DEV void gram_pipe_body(GramArgs<S> a, int bid, int k, uint32_t tbase, PipeBars& bars, const CUtensorMap* tmA,
+                           const CUtensorMap* tmB) {
   using Sh = PipeShape<NC>;
   using Sm = PipeSmem<NC, S>;
-  constexpr int T = Sh::T, TS = Sh::TS, UPT = Sh::UPT, KT = Sh::KT, LDS = Sm::LDS, SP = Sh::SP,
-                PLANE = Sh::PLANE, SBO = Sh::SBO, LBO = Sh::LBO, HALF = Sh::HALF, G = Sh::G;
+  constexpr int T = Sh::T, TS = Sh::TS, UPT = Sh::UPT, KT = Sh::KT, SP = Sh::SP, PLANE = Sh::PLANE,
+                SBO = Sh::SBO, LBO = Sh::LBO, HALF = Sh::HALF, G = Sh::G, RPB = Sm::RPB, NBOX = Sm::NBOX;
   constexpr uint32_t IDESC = umma_idesc_bf16(128, 128);
   extern __shared__ __align__(1024) unsigned char smem_umma[];
   unsigned char* smem = smem_umma;
@@ -1688,7 +1666,7 @@ QL_DEV void gram_pipe_body(GramArgs<S> a, int bid, int k, uint32_t tbase, PipeBa
   const bool control = warp == TS / 32;
 
   unsigned char* dig0 = smem + Sm::kOffDig;
-  S* raw0 = reinterpret_cast<S*>(smem + Sm::kOffRaw);
+  unsigned char* raw0 = smem + Sm::kOffRaw;  // 2 staged tiles of kRaw bytes
   float* pow2c = reinterpret_cast<float*>(smem + Sm::kOffPow);
   int* scale = reinterpret_cast<int*>(smem + Sm::kOffScale);  // running scale exponents (biased)
   int* colmax = reinterpret_cast<int*>(smem + Sm::kOffColmax);
@@ -1696,6 +1674,7 @@ QL_DEV void gram_pipe_body(GramArgs<S> a, int bid, int k, uint32_t tbase, PipeBa
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + Sm::kOffBar);  // [2] MMAs done, per digit buffer
   uint64_t* lbar = mbar + 2;                                          // [2] tile landed, per raw stage
   uint64_t* dbar = mbar + 4;                                          // [2] digits ready, per digit buffer
+  uint64_t* rbar = mbar + 6;                                          // [2] stage read, per raw stage
   int* ngrp = reinterpret_cast<int*>(smem + Sm::kOffSlot + 4);        // [2] tile opens a new group
   int* sfail = ngrp + 2;                                              // [2] where each role gave up
 
@@ -1714,9 +1693,9 @@ QL_DEV void gram_pipe_body(GramArgs<S> a, int bid, int k, uint32_t tbase, PipeBa
   tc_fence_after();
 
   const int64_t t0 = a.tiles * bid / k, t1 = a.tiles * (bid + 1) / k;
-  // a full tile of 16-byte aligned columns arrives by bulk copies; the slicers read any other
-  // tile (the ragged last one, or X not 16-byte aligned) from global memory themselves
-  auto tile_bulk = [&](int64_t t) { return a.bulk != 0 && (t + 1) * KT <= a.m; };
+  // with 16-byte aligned columns every tile arrives by tensor copies (rows past m read as
+  // zeros); otherwise the slicers read X from global memory themselves
+  auto tile_bulk = [&](int64_t) { return a.bulk != 0; };
 
   // this slicer's units of a tile: unit u = tid + TS uu covers rows r0..r0+7 of column c
   // (8 consecutive threads hold 8 consecutive columns, so their digit stores fill whole
@@ -1733,28 +1712,33 @@ QL_DEV void gram_pipe_body(GramArgs<S> a, int bid, int k, uint32_t tbase, PipeBa
   // read-out role: TMEM lane quarter qd, column part hh; lane L is plane offset kq, column li
   const int qd = warp & 3, hh = (warp >> 2) % (TS / 128);
   const int L = 32 * qd + lane, kq = L / NC, li = L % NC;
-  df acc[HALF];
-#pragma unroll
-  for (int j = 0; j < HALF; ++j) acc[j] = df{0.0f, 0.0f};
-  // FP64 level of the accumulators: this CTA's [NC columns][128 lanes] block of the
-  // workspace (L2-resident; each slicer touches only its own entries)
-  double* fb = a.w.fbuf + (size_t)bid * NC * 128;
+  // accumulators of this CTA's [NC columns][128 lanes] entries, in an L2-resident workspace
+  // block: the FP64 level, then the double-float sums (each slicer touches only its own)
+  double* fb = a.w.fbuf + (size_t)bid * NC * 128 * 2;
+  float2* fd = reinterpret_cast<float2*>(fb + (size_t)NC * 128);
   int erun[UPT];  // largest exponent each unit's column has shown this slicer (range record)
 #pragma unroll
   for (int uu = 0; uu < UPT; ++uu) erun[uu] = 0;
 
   if (control) {
-    // ---- control warp: copies two tiles ahead, then per tile: wait for its digits, copy the
-    // tile two ahead into the stage they were cut from, issue the MMAs and commit them
+    // ---- control warp: copies two tiles ahead, then per tile: once the slicers have read
+    // its stage, copy the tile two ahead into it; once its digits are ready, issue the MMAs
+    // and commit them
     bool ok = true;
     uint32_t pend = 0u, ppar = 0u;  // bit b: a copy into stage b in flight, and its phase parity
     auto copy = [&](int64_t t, int b) {
       if (!tile_bulk(t)) return;
-      S* stage = raw0 + (size_t)b * NC * LDS;
-      const int64_t row0 = t * KT;
-      if (lane == 0) mbar_arrive_expect_tx(&lbar[b], (uint32_t)(n * KT * sizeof(S)));
+      unsigned char* stage = raw0 + (size_t)b * Sm::kRaw;
+      const int row0 = (int)(t * KT);
+      if (lane == 0) {
+        mbar_arrive_expect_tx(&lbar[b], (uint32_t)(NBOX * n * 128));
+#pragma unroll 1
+        for (int kb = 0; kb < NBOX; ++kb) {
+          tma_load_2d(stage + (size_t)kb * NC * 128, tmA, row0 + kb * RPB, 0, &lbar[b]);
+          if (tmB) tma_load_2d(stage + (size_t)(kb * NC + a.src.nA) * 128, tmB, row0 + kb * RPB, 0, &lbar[b]);
+        }
+      }
       __syncwarp();
-      for (int cc = lane; cc < n; cc += 32) bulk_g2s(stage + cc * LDS, a.src.col(cc) + row0, KT * sizeof(S), &lbar[b]);
       pend |= 1u << b;
       ppar = (ppar & ~(1u << b)) | (bars.lpar & (1u << b));
       bars.lpar ^= 1u << b;
@@ -1763,14 +1747,18 @@ QL_DEV void gram_pipe_body(GramArgs<S> a, int bid, int k, uint32_t tbase, PipeBa
     if (t0 + 1 < t1) copy(t0 + 1, 1);
     for (int64_t t = t0; t < t1; ++t) {
       const int b = (int)((t - t0) & 1);
+      if (!__all_sync(0xffffffffu, mbar_wait_bounded(&rbar[b], (bars.mpar >> b) & 1u))) {
+        ok = false;
+        break;
+      }
+      pend &= ~(1u << b);  // the slicers have read stage b
+      if (t + 2 < t1) copy(t + 2, b);
       if (!__all_sync(0xffffffffu, mbar_wait_bounded(&dbar[b], (bars.mpar >> b) & 1u))) {
         ok = false;
         break;
       }
       bars.mpar ^= 1u << b;
-      pend &= ~(1u << b);  // the slicers have read stage b
       tc_fence_after();
-      if (t + 2 < t1) copy(t + 2, b);
       if (lane == 0) {
         const uint32_t fresh = (uint32_t)ngrp[b];
         // descriptor of plane 0, k-step 0; other planes and k-steps add (byte offset >> 4)
@@ -1804,7 +1792,10 @@ QL_DEV void gram_pipe_body(GramArgs<S> a, int bid, int k, uint32_t tbase, PipeBa
     int last_b = 0;       // digit buffer of the latest tile handed to the MMAs
     uint32_t cpar = 0u;   // bit b: phase parity of the MMAs of the latest tile on buffer b
 #pragma unroll
-    for (int j = 0; j < HALF; ++j) __stcg(fb + (size_t)(hh * HALF + j) * 128 + L, 0.0);
+    for (int j = 0; j < HALF; ++j) {
+      __stcg(fb + (size_t)(hh * HALF + j) * 128 + L, 0.0);
+      __stcg(fd + (size_t)(hh * HALF + j) * 128 + L, make_float2(0.0f, 0.0f));
+    }
 
     // fold the eight accumulator combinations into the double-float sums: combination tb of
     // this lane sits at column tb NC + j and weighs tb + kq (above 7: beyond the truncation,
@@ -1821,11 +1812,14 @@ QL_DEV void gram_pipe_body(GramArgs<S> a, int bid, int k, uint32_t tbase, PipeBa
         vm[tb] = w <= 7 ? 0xffffffffu : 0u;
       }
       const uint32_t lane_base = tbase + ((uint32_t)(32 * qd) << 16) + (uint32_t)(hh * HALF);
-#pragma unroll
+#pragma unroll 1
       for (int c0 = 0; c0 < HALF; c0 += 4) {
         uint32_t v[8][4];
 #pragma unroll
         for (int tb = 0; tb < 8; ++tb) tmem_ld(lane_base + (uint32_t)(tb * NC + c0), v[tb]);
+        float2 old[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) old[j] = __ldcg(fd + (size_t)(hh * HALF + c0 + j) * 128 + L);
         tmem_ld_wait();
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
@@ -1838,7 +1832,8 @@ QL_DEV void gram_pipe_body(GramArgs<S> a, int bid, int k, uint32_t tbase, PipeBa
             lo = __fadd_rn(lo, e2);
           }
           const float fj = pow2c[hh * HALF + c0 + j];
-          acc[c0 + j] = df_add(acc[c0 + j], df{hi * fj, lo * fj});
+          const df sum = df_add(df{old[j].x, old[j].y}, df{hi * fj, lo * fj});
+          __stcg(fd + (size_t)(hh * HALF + c0 + j) * 128 + L, make_float2(sum.hi, sum.lo));
         }
       }
     };
@@ -1865,7 +1860,8 @@ QL_DEV void gram_pipe_body(GramArgs<S> a, int bid, int k, uint32_t tbase, PipeBa
         e[uu] = 0;
         if (live_[uu]) {
           if (bulk) {
-            load8<S>(v[uu], raw0 + (size_t)b * NC * LDS + c_[uu] * LDS + r0_[uu]);
+            load8_swz<NC, S>(v[uu], raw0 + (size_t)b * Sm::kRaw, c_[uu], r0_[uu],
+                             c_[uu] == a.src.nA ? 0 : (c_[uu] & 7));
           } else {
             const S* col = a.src.col(c_[uu]);
             const int64_t row0 = t * KT + r0_[uu];
@@ -1881,6 +1877,10 @@ QL_DEV void gram_pipe_body(GramArgs<S> a, int bid, int k, uint32_t tbase, PipeBa
           for (int j = 0; j < 8; ++j) v[uu][j] = S(0);
         }
       }
+      // stage b is read: the control warp may copy the tile two ahead into it
+      fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&rbar[b]);
       // digit buffer b is free once the MMAs of tile t - 2 are done; a column whose tile
       // maximum exceeds its scale, or a full group, needs a read-out first (rare)
       const bool okw = i >= 2 ? mbar_wait_bounded(&mbar[b], (cpar >> b) & 1u) : true;
@@ -1901,12 +1901,14 @@ QL_DEV void gram_pipe_body(GramArgs<S> a, int bid, int k, uint32_t tbase, PipeBa
           tc_fence_after();
           readout();
           grp = 0;
-          if (++nread == Sh::DF_FLUSH) {  // double-float sums -> FP64 (L2)
-#pragma unroll
+          if (++nread == Sh::DF_FLUSH) {  // double-float sums -> FP64
+#pragma unroll 4
             for (int j = 0; j < HALF; ++j) {
               double* f = fb + (size_t)(hh * HALF + j) * 128 + L;
-              __stcg(f, __ldcg(f) + df_to_double(acc[j]));
-              acc[j] = df{0.0f, 0.0f};
+              float2* g = fd + (size_t)(hh * HALF + j) * 128 + L;
+              const float2 d2 = __ldcg(g);
+              __stcg(f, __ldcg(f) + df_to_double(df{d2.x, d2.y}));
+              __stcg(g, make_float2(0.0f, 0.0f));
             }
             nread = 0;
           }
@@ -1925,9 +1927,9 @@ QL_DEV void gram_pipe_body(GramArgs<S> a, int bid, int k, uint32_t tbase, PipeBa
 #pragma unroll
       for (int uu = 0; uu < UPT; ++uu) {
         const int cu = c_[uu], Es = live_[uu] ? scale[cu] : 0;
-        long long Nb[8];
+        unsigned long long Nb[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) Nb[j] = (live_[uu] ? fixed56<S>(v[uu][j], Es) : 0ll) + kDigitBias8;
+        for (int j = 0; j < 8; ++j) Nb[j] = biased_fixed56<S>(v[uu][j], Es);  // dead columns hold zeros
         put_planes8<NC, PLANE>(dig + (cu >> 3) * SBO + (r0_[uu] >> 3) * LBO + (cu & 7) * 16, Nb);
       }
       if (tid == 0) ngrp[b] = grp == 0 ? 1 : 0;
@@ -1969,9 +1971,11 @@ QL_DEV void gram_pipe_body(GramArgs<S> a, int bid, int k, uint32_t tbase, PipeBa
   // combine the plane offsets of each entry (FP64) and store this CTA's partial Gram matrix
   double* red = reinterpret_cast<double*>(smem + Sm::kOffDig);  // [lane L][column]
   if (!control) {
-#pragma unroll
-    for (int j = 0; j < HALF; ++j)
-      red[L * NC + hh * HALF + j] = __ldcg(fb + (size_t)(hh * HALF + j) * 128 + L) + df_to_double(acc[j]);
+#pragma unroll 4
+    for (int j = 0; j < HALF; ++j) {
+      const float2 d2 = __ldcg(fd + (size_t)(hh * HALF + j) * 128 + L);
+      red[L * NC + hh * HALF + j] = __ldcg(fb + (size_t)(hh * HALF + j) * 128 + L) + df_to_double(df{d2.x, d2.y});
+    }
   }
   __syncthreads();
   double* part = a.w.partials + (size_t)bid * NC * NC;
@@ -1986,11 +1990,13 @@ QL_DEV void gram_pipe_body(GramArgs<S> a, int bid, int k, uint32_t tbase, PipeBa
 }
 
 template <int NC, typename S>
-__global__ void __launch_bounds__(PipeShape<NC>::T, 1) gram_pipe_kernel(GramArgs<S> a) {
+__global__ void __launch_bounds__(PipeShape<NC>::T, 1)
+    gram_pipe_kernel(const __grid_constant__ GramArgs<S> a, const __grid_constant__ CUtensorMap tmA,
+                     const __grid_constant__ CUtensorMap tmB, int has_b) {
   extern __shared__ __align__(1024) unsigned char smem_umma[];
   const uint32_t tbase = pipe_cta_begin<NC, S>(smem_umma);
   PipeBars bars;
-  gram_pipe_body<NC, S>(a, blockIdx.x, gridDim.x, tbase, bars);
+  gram_pipe_body<NC, S>(a, blockIdx.x, gridDim.x, tbase, bars, &tmA, has_b ? &tmB : nullptr);
   tc_fence_before();
   __syncthreads();
   if ((threadIdx.x >> 5) == 0) tmem_dealloc(tbase, PipeShape<NC>::TCOLS);
@@ -2037,15 +2043,15 @@ ql_status gram_pipe_launch_one(const GramCall& c, const GramWs& w) {
   a.resnorm = c.resnorm;
   a.Rext = c.Rext;
   a.info = c.info;
-  {
-    auto aligned = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
-    bool b = aligned(c.A) && ((size_t)c.lda * sizeof(S)) % 16 == 0;
-    if (c.nA < c.n) b = b && aligned(c.b);
-    a.bulk = b ? 1 : 0;
-  }
+  CUtensorMap tmA{}, tmB{};
+  const bool has_b = c.nA < c.n;
+  a.bulk = pipe_tensor_maps(&tmA, has_b ? &tmB : nullptr, c.A, c.b, std::is_same<S, double>::value ? QL_F64 : QL_F32,
+                            c.m, c.nA, c.lda)
+               ? 1
+               : 0;
   a.mround = 2;
   count_launch();
-  kern<<<(int)g, Sh::T, Sm::kBytes, c.stream>>>(a);
+  kern<<<(int)g, Sh::T, Sm::kBytes, c.stream>>>(a, tmA, tmB, has_b ? 1 : 0);
   return cudaPeekAtLastError() == cudaSuccess ? QL_OK : QL_ERR_CUDA;
 }
 

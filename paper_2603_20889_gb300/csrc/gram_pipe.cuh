@@ -3,12 +3,12 @@
 //
 // The products are the exact bf16 digit products of gram_umma.cuh, arranged so that the
 // tensor core, the CUDA cores and the copy engine work on different tiles at once:
-//  * Warp roles.  Eight slicer warps cut tiles into digit planes and read the accumulators
+//  * Warp roles.  Sixteen slicer warps cut tiles into digit planes and read the accumulators
 //    out; one control warp issues the bulk copies (one column per lane, two tiles ahead) and
-//    the MMAs.  They meet only at mbarriers: "digits ready" per digit buffer (slicers ->
-//    control), "MMAs done" per digit buffer (tcgen05.commit -> slicers) and "tile landed" per
-//    raw stage (copy engine -> slicers).  The slicers vote among themselves on a named
-//    barrier, so the control warp never waits for them except on "digits ready".
+//    the MMAs.  They meet only at mbarriers: "stage read" per raw stage (slicers -> control:
+//    the next copy into it may start), "digits ready" per digit buffer (slicers -> control),
+//    "MMAs done" per digit buffer (tcgen05.commit -> slicers) and "tile landed" per raw stage
+//    (copy engine -> slicers).  The slicers vote among themselves on a named barrier.
 //  * A tile holds 4096 elements (KT = 4096 / NC rows).  Two raw stages and two digit
 //    buffers alternate: while the MMAs of tile t run, the slicers cut tile t + 1 and the
 //    copy of tile t + 2 is in flight.
@@ -26,11 +26,14 @@
 //    block of 128 accumulator columns at (p0 + q0) NC; lane k NC + i, column l NC + j of it
 //    carries weight p0 + q0 + k + l, so the combination tb = (p0 + q0) + l of a lane sits at
 //    column tb NC + j and weighs tb + k.  Combinations of weight above 7 are not read.
-//  * The read-out folds the blocks into double-float sums, which move into an FP64 level
-//    (an L2-resident workspace block per CTA) every few read-outs; at the end the CTA's
-//    partial Gram matrix goes to the workspace and the last CTA runs the common epilogue.
+//  * The read-out folds the blocks into double-float sums, kept with an FP64 level in an
+//    L2-resident workspace block per CTA (touched only at read-outs, so no registers hold
+//    them); the double-float sums move into the FP64 level every 16 read-outs.  At the end
+//    the CTA's partial Gram matrix goes to the workspace and the last CTA runs the common
+//    epilogue.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include "gram_tc.cuh"
@@ -40,9 +43,8 @@ namespace ql {
 
 template <int NC>
 struct PipeShape {
-  static constexpr int TS = 256;              // slicer threads: 8 warps, 2 per TMEM lane quarter
-  static constexpr int T = TS + 32;           // and the control warp (9 warps: at most 3 per
-                                              // SM sub-partition, so up to 168 registers each)
+  static constexpr int TS = 512;              // slicer threads: 16 warps, 4 per TMEM lane quarter
+  static constexpr int T = TS + 32;           // and the control warp (17 warps: up to 96 registers each)
   static constexpr int UPT = 512 / TS;        // 8-row units per slicer and tile
   static constexpr int KT = 4096 / NC;        // rows per tile: 64, 128, 256
   static constexpr int ND = 8;                // digit planes
@@ -56,7 +58,7 @@ struct PipeShape {
   static constexpr int G = 16;                // tiles summed in tensor memory per read-out
   static constexpr int SLACK = 2;             // bits of headroom above a new column maximum
   static constexpr int HALF = NC / (TS / 128);  // accumulator columns per slicer thread
-  static constexpr int DF_FLUSH = 4;          // read-outs per double-float -> FP64 move
+  static constexpr int DF_FLUSH = 16;         // read-outs per double-float -> FP64 move
   static_assert(NC == 16 || NC == 32 || NC == 64, "M = N = 128 needs 128 / NC stacked planes");
   static_assert(NC * KT / 8 == UPT * TS, "units of 8 rows of one column, UPT per slicer thread");
   static_assert((long long)G * KT * PAIRS_MAX * 4096 <= (1LL << 24), "exact FP32 digit sums");
@@ -65,18 +67,23 @@ struct PipeShape {
 template <int NC, typename S>
 struct PipeSmem {
   using Sh = PipeShape<NC>;
-  static constexpr int LDS = Sh::KT + 16 / (int)sizeof(S);  // padded staged column
+  // a staged tile is KT / RPB boxes of RPB rows (128 bytes) x NC columns, written by the
+  // tensor copy with the 128-byte swizzle: column c of box k is the 128-byte line
+  // k NC + c, whose 16-byte chunk q sits at chunk position q ^ (c & 7) (the right-hand
+  // side of least squares, a column of its own, is copied unswizzled)
+  static constexpr int RPB = 128 / (int)sizeof(S);            // rows per box
+  static constexpr int NBOX = Sh::KT / RPB;                   // boxes per tile
   static constexpr size_t kOffDig = 0;                       // 2 digit buffers (1024-aligned)
-  static constexpr size_t kRaw = sizeof(S) * (size_t)NC * LDS;
+  static constexpr size_t kRaw = sizeof(S) * (size_t)NC * Sh::KT;
   static constexpr size_t kOffRaw = kOffDig + 2 * (size_t)Sh::DBUF;  // 2 raw stages
   static constexpr size_t kOffPow = kOffRaw + 2 * kRaw;
   static constexpr size_t kOffScale = kOffPow + 4 * NC;       // running scale exponents
   static constexpr size_t kOffColmax = kOffScale + 4 * NC;
   static constexpr size_t kOffMisc = kOffColmax + 4 * NC;
-  // barriers: MMAs done [2], tile landed [2], digits ready [2]; then the TMEM slot, the
-  // new-group flags [2] and the failure flags of the two roles
+  // barriers: MMAs done [2], tile landed [2], digits ready [2], stage read [2]; then the
+  // TMEM slot, the new-group flags [2] and the failure flags of the two roles
   static constexpr size_t kOffBar = (kOffMisc + 64 * 4 + 15) / 16 * 16;
-  static constexpr size_t kOffSlot = kOffBar + 48;
+  static constexpr size_t kOffSlot = kOffBar + 64;
   static constexpr size_t kMain = kOffSlot + 32;
   static constexpr size_t kRed = 8 * (size_t)128 * NC;       // end of chunk: per-lane sums (in the digits)
   static constexpr size_t kEpi = 8 * (4 * (size_t)NC * (NC + 1) + 8 * (NC + 1)) + 64 * 4 + 16;
@@ -89,7 +96,7 @@ struct PipeSmem {
 // of each barrier pair's next phase, and whether every bounded wait so far succeeded
 // (uniform across the CTA).  Each thread keeps its own copy; a role only uses its own bits.
 struct PipeBars {
-  uint32_t mpar = 0;  // bit b: next phase of "MMAs done" b (slicers) / "digits ready" b (control)
+  uint32_t mpar = 0;  // bit b: next phase of "MMAs done" b (slicers) / "stage read" and "digits ready" b (control)
   uint32_t lpar = 0;  // bit b: next phase of "tile landed" b
   bool ok = true;
 };
@@ -102,7 +109,7 @@ QL_DEV uint32_t pipe_cta_begin(unsigned char* smem) {
   if (threadIdx.x == 0) {
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + Sm::kOffBar);
     for (int i = 0; i < 4; ++i) mbar_init(bar + i, 1);
-    for (int i = 4; i < 6; ++i) mbar_init(bar + i, PipeShape<NC>::TS / 32);  // one arrival per slicer warp
+    for (int i = 4; i < 8; ++i) mbar_init(bar + i, PipeShape<NC>::TS / 32);  // one arrival per slicer warp
   }
   tc_fence_before();
   __syncthreads();
@@ -136,6 +143,32 @@ QL_DEV bool slicer_and(bool p) {
   return r != 0;
 }
 
+// One box of a rank-2 tensor map (x = row, innermost; y = column) into shared memory, its
+// bytes counted on the mbarrier.  x must be a multiple of 16 bytes' worth of elements.
+QL_DEV void tma_load_2d(void* dst, const CUtensorMap* tm, int x, int y, uint64_t* mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(
+          smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(smem_addr(mbar))
+      : "memory");
+}
+
+// The 8 rows r0..r0+7 of column c of a staged tile (see PipeSmem: boxes of RPB rows, 128-byte
+// swizzle; swz = c & 7, or 0 for the unswizzled right-hand-side column); r0 is a multiple of 8.
+template <int NC, typename S>
+QL_DEV void load8_swz(S (&v)[8], const unsigned char* stage, int c, int r0, int swz) {
+  constexpr int RPB = 128 / (int)sizeof(S), EPC = 16 / (int)sizeof(S);  // rows per box, per chunk
+  const unsigned char* line = stage + (size_t)((r0 / RPB) * NC + c) * 128;
+  const int q0 = (r0 % RPB) / EPC;
+#pragma unroll
+  for (int q = 0; q < 8 / EPC; ++q) {
+    const float4 t = *reinterpret_cast<const float4*>(line + (((q0 + q) ^ swz) << 4));
+    const S* e = reinterpret_cast<const S*>(&t);
+#pragma unroll
+    for (int j = 0; j < EPC; ++j) v[q * EPC + j] = e[j];
+  }
+}
+
 // Sign, biased double exponent and 53-bit significand of a stored element (0 for zero).
 QL_DEV void split_elem(double x, unsigned& neg, int& E, unsigned long long& sig) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
@@ -156,47 +189,58 @@ QL_DEV int elem_exponent(float x) {
   return ef == 0 ? 0 : ef + 896;
 }
 
-// Round-to-nearest (ties to even) fixed point N = rint(x 2^(55 - e)) of an element relative
-// to the scale exponent Es >= E (e = Es - 1022, |x| < 2^e); |N| < 2^55.
+// Eight balanced base-128 digits of a signed fixed-point value |N| < 2^55.  With
+// Nb = N + kDigitBias8 (64 added to every digit position, the top one included), every
+// digit is a bit field of Nb: digit p >= 1 is ((Nb >> 7 (7 - p)) & 127) - 64 and digit 0 is
+// (Nb >> 49) - 64; all lie in [-64, 64] (Nb is positive and below 2^57).
+constexpr unsigned long long kDigitBias8 =
+    64ULL * ((1ULL << 49) + (1ULL << 42) + (1ULL << 35) + (1ULL << 28) + (1ULL << 21) + (1ULL << 14) + (1ULL << 7) + 1ULL);
+
+// Nb = N + kDigitBias8 of one element, N = rint(x 2^(55 - e)) its round-to-nearest (ties to
+// even) fixed point relative to the scale exponent Es >= E (e = Es - 1022, |x| < 2^e, so
+// |N| < 2^55).  The common case, a shift of at most 31 bits, runs on 32-bit words (one
+// funnel shift, and the dropped word decides the rounding); smaller elements take the
+// 64-bit form.
 template <typename S>
-QL_DEV long long fixed56(S x, int Es) {
+QL_DEV unsigned long long biased_fixed56(S x, int Es) {
   unsigned neg;
   int E;
   unsigned long long sig;
   split_elem(x, neg, E, sig);
-  if (E == 0) return 0;
-  const int sh = Es - E - 2;  // x 2^(55 - e) = sig 2^-sh
+  const int sh = Es - E - 2;
   unsigned long long q;
-  if (sh <= 0) {
-    q = sig << (-sh);  // E >= Es - 2: exact
+  if (E == 0) {
+    q = 0ull;
+  } else if (sh <= 31) {
+    const unsigned sh_ = (unsigned)(sig >> 32), sl = (unsigned)sig;
+    if (sh <= 0) {
+      q = sig << (-sh);  // E >= Es - 2: exact
+    } else {
+      const unsigned ql = __funnelshift_r(sl, sh_, sh), qh = sh_ >> sh;
+      const unsigned rem = sl << (32 - sh), half = 0x80000000u;
+      const unsigned up = (rem > half || (rem == half && (ql & 1u))) ? 1u : 0u;
+      q = (((unsigned long long)qh << 32) | ql) + up;
+    }
   } else if (sh >= 54) {
-    return 0;          // below a quarter of the last place
+    q = 0ull;  // below a quarter of the last place
   } else {
     q = sig >> sh;
     const unsigned long long rem = sig << (64 - sh), half = 1ull << 63;
     q += (rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull;
   }
-  return neg ? -(long long)q : (long long)q;
+  const unsigned long long m = neg ? ~0ull : 0ull;
+  return (q ^ m) + (kDigitBias8 + (neg ? 1ull : 0ull));  // N + bias, N = +-q
 }
 
-// Eight balanced base-128 digits of a signed fixed-point value |N| < 2^55: with
-// Nb = N + kDigitBias8 (64 added to every position below the top one), digit p >= 1 is
-// ((Nb >> 7 (7 - p)) & 127) - 64 and digit 0 is (Nb >> 49); all lie in [-64, 64].
-constexpr long long kDigitBias8 = 64LL * ((1LL << 42) + (1LL << 35) + (1LL << 28) + (1LL << 21) + (1LL << 14) +
-                                          (1LL << 7) + 1LL);
-// digit p plus 64, in [0, 128]
+// Digit p of two elements (rows r, r + 1) as one bf16x2 word (row r in the lower half):
+// the fields f (digit + 64, in [0, 128]) become bf16(128 + f) by their bits 0x4300 + f,
+// and subtracting 192 leaves the digit exactly.
 template <int P>
-QL_DEV unsigned digit_field8(long long Nb) {
-  if constexpr (P == 0) {
-    return (unsigned)((int)(Nb >> 49) + 64);
-  } else {
-    return (unsigned)(Nb >> (7 * (7 - P))) & 127u;
-  }
-}
-// Two digits (given as digit + 64 in [0, 128]) as a bf16x2 register: bf16(128 + f) has the
-// bits 0x4300 + f, and subtracting 192 leaves f - 64 exactly (lo in the lower half).
-QL_DEV unsigned bf16x2_of_fields(unsigned fa, unsigned fb) {
-  const unsigned w = (0x4300u + fa) | ((0x4300u + fb) << 16);
+QL_DEV unsigned digit_word(unsigned long long A, unsigned long long B) {
+  constexpr int SH = 7 * (7 - P);
+  constexpr unsigned MASK = P == 0 ? 0x00ff00ffu : 0x007f007fu;
+  const unsigned fa = (unsigned)(A >> SH), fb = (unsigned)(B >> SH);
+  const unsigned w = (__byte_perm(fa, fb, 0x5410) & MASK) | 0x43004300u;
   const __nv_bfloat162 r =
       __hsub2(*reinterpret_cast<const __nv_bfloat162*>(&w), __floats2bfloat162_rn(192.0f, 192.0f));
   return *reinterpret_cast<const unsigned*>(&r);

@@ -4,6 +4,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "../../include/qless.h"
@@ -87,6 +88,13 @@ bool tc_gram_enabled();
 // First Gram pass of the 16-, 32- and 64-column classes on the pipelined tcgen05 kernel
 // (default; QL_GRAM_PIPE=0 selects the per-tile kernels, for comparison).
 bool pipe_gram_enabled();
+// Tensor maps of the columns of [A b] for the pipelined Gram pass: A as a rank-2 tensor (rows
+// innermost, stride lda; boxes of 128 bytes of rows x all its columns, 128-byte swizzle) and
+// b as one unswizzled column; rows past m read as zeros.  tmB may be null (no b).  False, with the maps left
+// unset, if the data does not allow tensor copies (a column not 16-byte aligned, m >= 2^31)
+// or the driver offers no encoder; the caller then reads X without them.
+bool pipe_tensor_maps(CUtensorMap* tmA, CUtensorMap* tmB, const void* A, const void* b, int dtype, int64_t m, int nA,
+                      int64_t lda);
 
 // Thread-layout variant of the TSQR kernels (environment QL_TSQR_CFG, 0 = default).
 int tsqr_variant();
