@@ -42,10 +42,9 @@ PASSES = {"tsqr": 1, "cholqr2": 2, "svqb2": 2}
 # roofline's "traffic" is this times m for the dominant call, null where no capture of the
 # current kernel exists.
 MEASURED_TRAFFIC_PER_ROW = {
-    ("tsqr", 64): (1.074283e9 + 3.643648e6) / 2 ** 21,     # tsqr_kernel<64, 16, 16, 256>, m = 2^21
-    ("tsqr", 8): (1.073880e9 + 3.648512e6) / 2 ** 24,      # tsqr_kernel<8>, m = 2^24
-    ("cholqr2", 64): (2.147588e9 + 3.204096e6) / 2 ** 22,  # gram_umma_kernel<64> first pass, m = 2^22
-    ("svqb2", 32): (1.074148e9 + 3.180544e6) / 2 ** 22,    # gram_tc_kernel<32> first pass, m = 2^22
+    ("tsqr", 64): (1.074413e9 + 3.693568e6) / 2 ** 21,       # tsqr_kernel<64, 16, 16, 256>, m = 2^21
+    ("tsqr", 4): (536.98944e6 + 3.195648e6) / 2 ** 24,       # tsqr_kernel<4, 1, 8, 128>, m = 2^24
+    ("cholqr2", 64): (2.256619e9 + 174.161664e6) / 2 ** 22,  # gram_pipe_kernel<64> (first pass), m = 2^22
 }
 
 
