@@ -23,6 +23,14 @@ bool pipe_gram_enabled() {
   return on;
 }
 
+bool pipe_gram2_enabled() {
+  static const bool on = [] {
+    const char* v = std::getenv("QL_GRAM_PIPE2");
+    return !(v && v[0] == '0');
+  }();
+  return on;
+}
+
 bool pipe_tensor_maps(CUtensorMap* tmA, CUtensorMap* tmB, const void* A, const void* b, int dtype, int64_t m, int nA,
                       int64_t lda) {
   using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,

@@ -1652,11 +1652,28 @@ QL_DEV void put_planes8(unsigned char* base, const unsigned long long (&Nb)[8]) 
   if constexpr (P + 1 < 8) put_planes8<NC, PLANE, P + 1>(base, Nb);
 }
 
-template <int NC, typename S>
+// Digits P.. of one element (biased fixed point Nb, see biased_fixed56) into their planes,
+// one 2-byte store per plane.
+template <int PLANE, int P = 0>
+QL_DEV void put_digits8_one(unsigned char* p0, unsigned long long Nb) {
+  *reinterpret_cast<unsigned short*>(p0 + P * PLANE) = (unsigned short)(digit_word<P>(Nb, Nb) & 0xffffu);
+  if constexpr (P + 1 < 8) put_digits8_one<PLANE, P + 1>(p0, Nb);
+}
+
+// XF = kXNone: the first pass (C = X^T X).  XF = kXUpper / kXFull (n <= 32): a later pass of
+// Cholesky-QR2 / shifted Cholesky-QR3 (M = R1^{-1}, upper triangular) or SVQB2 (M = B1):
+// C = Y^T Y with Y = X M formed tile by tile and never stored.  The slicer warps then cut X
+// into seven digits at the whole matrix's column scale (the first pass recorded it), form
+// Y = X M' (M' = diag(2^e_k) M) on mma.sync from those digits and the M' digits (B
+// fragments in shared memory), fold the seven weights of each element into a double-float
+// and cut Y into the eight digits of the Gram, as the first pass cuts X; the control warp,
+// the copies and the tensor-memory sums are the first pass's.
+template <int NC, typename S, int XF = kXNone>
 QL_DEV void gram_pipe_body(GramArgs<S> a, int bid, int k, uint32_t tbase, PipeBars& bars, const CUtensorMap* tmA,
                            const CUtensorMap* tmB) {
   using Sh = PipeShape<NC>;
-  using Sm = PipeSmem<NC, S>;
+  using Sm = PipeSmem<NC, S, XF>;
+  static_assert(XF == kXNone || NC <= 32, "later passes: the M' fragments of n <= 32 columns");
   constexpr int T = Sh::T, TS = Sh::TS, UPT = Sh::UPT, KT = Sh::KT, SP = Sh::SP, PLANE = Sh::PLANE,
                 SBO = Sh::SBO, LBO = Sh::LBO, HALF = Sh::HALF, G = Sh::G, RPB = Sm::RPB, NBOX = Sm::NBOX;
   constexpr uint32_t IDESC = umma_idesc_bf16(128, 128);
@@ -1685,6 +1702,66 @@ QL_DEV void gram_pipe_body(GramArgs<S> a, int bid, int k, uint32_t tbase, PipeBa
     pow2c[i] = 0.0f;
   }
   if (tid < 2) sfail[tid] = 0;
+  bool skip_tiles = false;
+  if constexpr (XF != kXNone) {
+    int* gexp = reinterpret_cast<int*>(smem + Sm::kOffGexp);  // X's column exponents (whole matrix)
+    int* fexp = reinterpret_cast<int*>(smem + Sm::kOffFexp);  // M''s column exponents
+    int* entry = reinterpret_cast<int*>(smem + Sm::kOffEntry);
+    uint2* bqs = reinterpret_cast<uint2*>(smem + Sm::kOffBq);
+    // the entry conditions of every later pass, decided once for the whole CTA
+    if (tid == 0) {
+      int e = 0;
+      if (*(volatile int*)&a.w.flags[0] != 0) e = 1;       // the FP64 launches redo the call
+      else if (*(volatile int*)&a.w.flags[1] != 0) e = 2;  // the first pass broke down
+      entry[0] = e;
+    }
+    __syncthreads();
+    const int e0 = entry[0];
+    if (e0 == 2 && bid == 0) write_nan_outputs(a, T);
+    if (e0 != 0) return;
+    for (int i = tid; i < NC; i += T) gexp[i] = i < n ? __ldcg(&a.w.flags[64 + i]) : 0;
+    __syncthreads();
+    const double* M = a.w.keep + (size_t)n * n;  // the previous pass's M (row-major, ld n)
+    auto mprime = [&](int kk, int j) -> double {  // M'(kk, j), zero outside the used part
+      if (kk >= n || j >= n || (XF == kXUpper && kk > j)) return 0.0;
+      const int ek = gexp[kk];
+      return ek > 0 ? __ldcg(M + (size_t)kk * n + j) * __longlong_as_double((long long)(ek + 1) << 52) : 0.0;
+    };
+    for (int j = tid; j < NC; j += T) {
+      int F = 0;
+      for (int kk = 0; kk < NC; ++kk) F = max(F, (int)((__double_as_longlong(mprime(kk, j)) >> 52) & 0x7ff));
+      fexp[j] = F;
+    }
+    __syncthreads();
+    bool bad = false;  // the fold scales of Y must stay normal floats
+    for (int j = tid; j < NC; j += T) {
+      const int F = fexp[j], f = F - 1022;
+      if (F > 0 && (f < -70 || f > 100)) bad = true;
+    }
+    if (__syncthreads_or(bad)) {  // out of the double-float range: the FP64 launches redo it
+      if (tid == 0) atomicOr(&a.w.flags[0], 1);
+      skip_tiles = true;
+    }
+    // B fragments of M' for mma m16n8k16: lane (g, t4) of 8-column block cb holds rows
+    // k = 16 ks + 2 t4 + {0, 1} (first word) and k + 8 (second word) of column 8 cb + g,
+    // seven balanced digits of the 48-bit fixed point relative to that column's exponent
+    constexpr int NCB = Sm::NCB, KSTEPS = Sm::KSTEPS;
+    for (int it = tid; it < NCB * KSTEPS * 32; it += T) {
+      const int ln = it & 31, ks = (it >> 5) % KSTEPS, cb = (it >> 5) / KSTEPS;
+      const int j = cb * 8 + (ln >> 2), t4 = ln & 3, F = fexp[j];
+      long long Nb[4];
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        const int kk = 16 * ks + 2 * t4 + (h & 1) + 8 * (h >> 1);
+        Nb[h] = (F > 0 ? fixed48_of_double(mprime(kk, j), F) : 0ll) + kDigitBias;
+      }
+#pragma unroll
+      for (int q = 0; q < 7; ++q)
+        bqs[((cb * KSTEPS + ks) * 7 + q) * 32 + ln] =
+            make_uint2(bf16x2_of_ints(balanced_digit_rt(Nb[0], q), balanced_digit_rt(Nb[1], q)),
+                       bf16x2_of_ints(balanced_digit_rt(Nb[2], q), balanced_digit_rt(Nb[3], q)));
+    }
+  }
   // the previous work item's generic writes (its reduction and epilogue) come before this
   // item's bulk copies and MMA operand reads
   fence_proxy_async_smem();
@@ -1692,7 +1769,7 @@ QL_DEV void gram_pipe_body(GramArgs<S> a, int bid, int k, uint32_t tbase, PipeBa
   __syncthreads();
   tc_fence_after();
 
-  const int64_t t0 = a.tiles * bid / k, t1 = a.tiles * (bid + 1) / k;
+  const int64_t t0 = a.tiles * bid / k, t1 = skip_tiles ? t0 : a.tiles * (bid + 1) / k;
   // with 16-byte aligned columns every tile arrives by tensor copies (rows past m read as
   // zeros); otherwise the slicers read X from global memory themselves
   auto tile_bulk = [&](int64_t) { return a.bulk != 0; };
@@ -1852,95 +1929,268 @@ QL_DEV void gram_pipe_body(GramArgs<S> a, int bid, int k, uint32_t tbase, PipeBa
         fail_where = 1;
         break;
       }
-      S v[UPT][8];
-      int e[UPT];
-      bool over = false;
-#pragma unroll
-      for (int uu = 0; uu < UPT; ++uu) {
-        e[uu] = 0;
-        if (live_[uu]) {
-          if (bulk) {
-            load8_swz<NC, S>(v[uu], raw0 + (size_t)b * Sm::kRaw, c_[uu], r0_[uu],
-                             c_[uu] == a.src.nA ? 0 : (c_[uu] & 7));
+      if constexpr (XF == kXNone) {
+        S v[UPT][8];
+        int e[UPT];
+        bool over = false;
+  #pragma unroll
+        for (int uu = 0; uu < UPT; ++uu) {
+          e[uu] = 0;
+          if (live_[uu]) {
+            if (bulk) {
+              load8_swz<NC, S>(v[uu], raw0 + (size_t)b * Sm::kRaw, c_[uu], r0_[uu],
+                               c_[uu] == a.src.nA ? 0 : (c_[uu] & 7));
+            } else {
+              const S* col = a.src.col(c_[uu]);
+              const int64_t row0 = t * KT + r0_[uu];
+  #pragma unroll
+              for (int j = 0; j < 8; ++j) v[uu][j] = row0 + j < a.m ? __ldg(col + row0 + j) : S(0);
+            }
+  #pragma unroll
+            for (int j = 0; j < 8; ++j) e[uu] = max(e[uu], elem_exponent(v[uu][j]));
+            erun[uu] = max(erun[uu], e[uu]);
+            over = over || e[uu] > scale[c_[uu]];
           } else {
-            const S* col = a.src.col(c_[uu]);
-            const int64_t row0 = t * KT + r0_[uu];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) v[uu][j] = row0 + j < a.m ? __ldg(col + row0 + j) : S(0);
+  #pragma unroll
+            for (int j = 0; j < 8; ++j) v[uu][j] = S(0);
           }
-#pragma unroll
-          for (int j = 0; j < 8; ++j) e[uu] = max(e[uu], elem_exponent(v[uu][j]));
-          erun[uu] = max(erun[uu], e[uu]);
-          over = over || e[uu] > scale[c_[uu]];
-        } else {
-#pragma unroll
-          for (int j = 0; j < 8; ++j) v[uu][j] = S(0);
         }
-      }
-      // stage b is read: the control warp may copy the tile two ahead into it
-      fence_proxy_async_smem();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&rbar[b]);
-      // digit buffer b is free once the MMAs of tile t - 2 are done; a column whose tile
-      // maximum exceeds its scale, or a full group, needs a read-out first (rare)
-      const bool okw = i >= 2 ? mbar_wait_bounded(&mbar[b], (cpar >> b) & 1u) : true;
-      const bool full = grp >= G;
-      if (slicer_or<TS>(over || !okw) || full) {
+        // stage b is read: the control warp may copy the tile two ahead into it
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&rbar[b]);
+        // digit buffer b is free once the MMAs of tile t - 2 are done; a column whose tile
+        // maximum exceeds its scale, or a full group, needs a read-out first (rare)
+        const bool okw = i >= 2 ? mbar_wait_bounded(&mbar[b], (cpar >> b) & 1u) : true;
+        const bool full = grp >= G;
+        if (slicer_or<TS>(over || !okw) || full) {
+          if (!slicer_and<TS>(okw)) {  // the tensor core did not finish: FP64 redoes the call
+            ok = false;
+            fail_where = 2;
+            break;
+          }
+          const bool anyover = slicer_or<TS>(over);
+          if ((anyover || full) && grp > 0) {  // read the sums out before their scale changes or they could round
+            if (!slicer_and<TS>(mbar_wait_bounded(&mbar[last_b], (cpar >> last_b) & 1u))) {
+              ok = false;
+              fail_where = 2;
+              break;
+            }
+            tc_fence_after();
+            readout();
+            grp = 0;
+            if (++nread == Sh::DF_FLUSH) {  // double-float sums -> FP64
+  #pragma unroll 4
+              for (int j = 0; j < HALF; ++j) {
+                double* f = fb + (size_t)(hh * HALF + j) * 128 + L;
+                float2* g = fd + (size_t)(hh * HALF + j) * 128 + L;
+                const float2 d2 = __ldcg(g);
+                __stcg(f, __ldcg(f) + df_to_double(df{d2.x, d2.y}));
+                __stcg(g, make_float2(0.0f, 0.0f));
+              }
+              nread = 0;
+            }
+            slicer_sync<TS>();  // every read of the blocks and of the old scales is done
+          }
+  #pragma unroll
+          for (int uu = 0; uu < UPT; ++uu)
+            if (live_[uu] && e[uu] > scale[c_[uu]]) atomicMax(&scale[c_[uu]], e[uu] + Sh::SLACK);
+          slicer_sync<TS>();
+          for (int cc = tid; cc < NC; cc += TS) {
+            const int s = scale[cc];
+            pow2c[cc] = s > 0 ? __int_as_float(max(1, min(254, s - 895)) << 23) : 0.0f;  // 2^(s - 1022)
+          }
+        }
+        // eight digits of every element into the core-matrix layout of buffer b
+  #pragma unroll
+        for (int uu = 0; uu < UPT; ++uu) {
+          const int cu = c_[uu], Es = live_[uu] ? scale[cu] : 0;
+          unsigned long long Nb[8];
+  #pragma unroll
+          for (int j = 0; j < 8; ++j) Nb[j] = biased_fixed56<S>(v[uu][j], Es);  // dead columns hold zeros
+          put_planes8<NC, PLANE>(dig + (cu >> 3) * SBO + (r0_[uu] >> 3) * LBO + (cu & 7) * 16, Nb);
+        }
+        if (tid == 0) ngrp[b] = grp == 0 ? 1 : 0;
+        fence_proxy_async_smem();  // the digit planes are read by the tensor core
+        tc_fence_before();         // the read-out's TMEM loads come before the next MMAs
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&dbar[b]);
+        cpar = (cpar & ~(1u << b)) | (bars.mpar & (1u << b));
+        bars.mpar ^= 1u << b;
+        last_b = b;
+        ++grp;
+      } else {
+        // ---- later pass: Y = X M' for this tile, then Y's digits
+        const int* gexp = reinterpret_cast<const int*>(smem + Sm::kOffGexp);
+        const int* fexp = reinterpret_cast<const int*>(smem + Sm::kOffFexp);
+        const uint2* bqs = reinterpret_cast<const uint2*>(smem + Sm::kOffBq);
+        constexpr int NCB = Sm::NCB, KSTEPS = Sm::KSTEPS;
+        static_assert(NCB * (KT / 16) == 2 * (TS / 32), "two 16 x 8 blocks of Y per slicer warp");
+        // buffer b takes X's digits first: the MMAs of tile t - 2 must be done with it
+        const bool okw = i >= 2 ? mbar_wait_bounded(&mbar[b], (cpar >> b) & 1u) : true;
         if (!slicer_and<TS>(okw)) {  // the tensor core did not finish: FP64 redoes the call
           ok = false;
           fail_where = 2;
           break;
         }
-        const bool anyover = slicer_or<TS>(over);
-        if ((anyover || full) && grp > 0) {  // read the sums out before their scale changes or they could round
-          if (!slicer_and<TS>(mbar_wait_bounded(&mbar[last_b], (cpar >> last_b) & 1u))) {
-            ok = false;
-            fail_where = 2;
-            break;
-          }
-          tc_fence_after();
-          readout();
-          grp = 0;
-          if (++nread == Sh::DF_FLUSH) {  // double-float sums -> FP64
-#pragma unroll 4
-            for (int j = 0; j < HALF; ++j) {
-              double* f = fb + (size_t)(hh * HALF + j) * 128 + L;
-              float2* g = fd + (size_t)(hh * HALF + j) * 128 + L;
-              const float2 d2 = __ldcg(g);
-              __stcg(f, __ldcg(f) + df_to_double(df{d2.x, d2.y}));
-              __stcg(g, make_float2(0.0f, 0.0f));
+        // seven balanced digits of X at the whole matrix's column scale, 8 rows of one
+        // column per unit (the core-matrix layout of the Gram digits)
+#pragma unroll
+        for (int uu = 0; uu < UPT; ++uu) {
+          const int cu = c_[uu], em = live_[uu] ? gexp[cu] : 0;
+          S xv[8];
+          if (live_[uu]) {
+            if (bulk) {
+              load8_swz<NC, S>(xv, raw0 + (size_t)b * Sm::kRaw, cu, r0_[uu], cu == a.src.nA ? 0 : (cu & 7));
+            } else {
+              const S* col = a.src.col(cu);
+              const int64_t row0 = t * KT + r0_[uu];
+#pragma unroll
+              for (int j = 0; j < 8; ++j) xv[j] = row0 + j < a.m ? __ldg(col + row0 + j) : S(0);
             }
-            nread = 0;
+          } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) xv[j] = S(0);
           }
-          slicer_sync<TS>();  // every read of the blocks and of the old scales is done
+          long long Nb[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            if constexpr (sizeof(S) == 8) {
+              Nb[j] = (em > 0 ? fixed48_of_double((double)xv[j], em) : 0ll) + kDigitBias;
+            } else {
+              Nb[j] = (em > 0 ? fixed48_of_float((float)xv[j], em - 896) : 0ll) + kDigitBias;
+            }
+          }
+          unsigned char* base = dig + (cu >> 3) * SBO + (r0_[uu] >> 3) * LBO + (cu & 7) * 16;
+#pragma unroll
+          for (int p = 0; p < 7; ++p) {
+            uint4 wv;
+            wv.x = bf16x2_of_ints(balanced_digit_rt(Nb[0], p), balanced_digit_rt(Nb[1], p));
+            wv.y = bf16x2_of_ints(balanced_digit_rt(Nb[2], p), balanced_digit_rt(Nb[3], p));
+            wv.z = bf16x2_of_ints(balanced_digit_rt(Nb[4], p), balanced_digit_rt(Nb[5], p));
+            wv.w = bf16x2_of_ints(balanced_digit_rt(Nb[6], p), balanced_digit_rt(Nb[7], p));
+            *reinterpret_cast<uint4*>(base + p * PLANE) = wv;
+          }
         }
+        // stage b is read: the control warp may copy the tile two ahead into it
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&rbar[b]);
+        slicer_sync<TS>();  // X's digits are in place
+        // Y = X M' on mma.sync: this warp's 8-column block cb and two 16-row blocks; per
+        // block the 28 digit pairs (p + q <= 6) accumulate exactly in FP32 per weight
+        const int g = lane >> 2, t4 = lane & 3, cb = warp % NCB;
+        const int ksw = XF == kXUpper ? (cb >> 1) + 1 : KSTEPS;  // M' upper triangular: k <= j
+        df y[2][4];
 #pragma unroll
-        for (int uu = 0; uu < UPT; ++uu)
-          if (live_[uu] && e[uu] > scale[c_[uu]]) atomicMax(&scale[c_[uu]], e[uu] + Sh::SLACK);
-        slicer_sync<TS>();
-        for (int cc = tid; cc < NC; cc += TS) {
-          const int s = scale[cc];
-          pow2c[cc] = s > 0 ? __int_as_float(max(1, min(254, s - 895)) << 23) : 0.0f;  // 2^(s - 1022)
+        for (int bi = 0; bi < 2; ++bi) {
+          const int rb = warp / NCB + bi * (16 / NCB);
+          float ac[7][4];
+#pragma unroll
+          for (int d = 0; d < 7; ++d)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) ac[d][e] = 0.0f;
+#pragma unroll
+          for (int ks = 0; ks < KSTEPS; ++ks) {
+            if (ks < ksw) {
+              uint2 bw[7];
+#pragma unroll
+              for (int q = 0; q < 7; ++q) bw[q] = bqs[((cb * KSTEPS + ks) * 7 + q) * 32 + lane];
+              // ldmatrix .trans of core matrix (column group 2 ks + K, row group 2 rb + R)
+              const unsigned char* ap =
+                  dig + (2 * ks + (lane >> 4)) * SBO + (2 * rb + ((lane >> 3) & 1)) * LBO + (lane & 7) * 16;
+#pragma unroll
+              for (int p = 0; p < 7; ++p) {
+                unsigned a0, a1, a2, a3;
+                ldsm_x4_t(a0, a1, a2, a3, ap + p * PLANE);
+#pragma unroll
+                for (int q = 0; q + p < 7; ++q) mma_bf16(ac[p + q], a0, a1, a2, a3, bw[q].x, bw[q].y);
+              }
+            }
+          }
+          // fold the seven weights (smallest first) into one double-float per element;
+          // weight d of column j weighs 2^(f_j - 12 - 7 d), f_j = fexp[j] - 1022
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int F = fexp[cb * 8 + 2 * t4 + (e & 1)], f = F - 1022;
+            float hi = ac[6][e] * __int_as_float((f - kDigitScaleLog2 - 42 + 127) << 23), lo = 0.0f;
+#pragma unroll
+            for (int d = 5; d >= 0; --d) {
+              float s2, e2;
+              two_sum(hi, ac[d][e] * __int_as_float((f - kDigitScaleLog2 - 7 * d + 127) << 23), s2, e2);
+              hi = s2;
+              lo = __fadd_rn(lo, e2);
+            }
+            y[bi][e] = F > 0 ? df_make(hi, lo) : df{0.0f, 0.0f};
+          }
         }
-      }
-      // eight digits of every element into the core-matrix layout of buffer b
+        slicer_sync<TS>();  // every read of X's digits is done: buffer b takes Y's digits next
+        // Y against the running column scales (this lane holds columns c0 and c0 + 1)
+        const int c0 = cb * 8 + 2 * t4;
+        double yd[2][4];
+        int ey[2] = {0, 0};
 #pragma unroll
-      for (int uu = 0; uu < UPT; ++uu) {
-        const int cu = c_[uu], Es = live_[uu] ? scale[cu] : 0;
-        unsigned long long Nb[8];
+        for (int bi = 0; bi < 2; ++bi)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) Nb[j] = biased_fixed56<S>(v[uu][j], Es);  // dead columns hold zeros
-        put_planes8<NC, PLANE>(dig + (cu >> 3) * SBO + (r0_[uu] >> 3) * LBO + (cu & 7) * 16, Nb);
+          for (int e = 0; e < 4; ++e) {
+            yd[bi][e] = df_to_double(y[bi][e]);
+            ey[e & 1] = max(ey[e & 1], elem_exponent(yd[bi][e]));
+          }
+        const bool over = ey[0] > scale[c0] || ey[1] > scale[c0 + 1];
+        const bool full = grp >= G;
+        if (slicer_or<TS>(over) || full) {
+          if (grp > 0) {  // read the sums out before their scale changes or they could round
+            if (!slicer_and<TS>(mbar_wait_bounded(&mbar[last_b], (cpar >> last_b) & 1u))) {
+              ok = false;
+              fail_where = 2;
+              break;
+            }
+            tc_fence_after();
+            readout();
+            grp = 0;
+            if (++nread == Sh::DF_FLUSH) {  // double-float sums -> FP64
+#pragma unroll 4
+              for (int j = 0; j < HALF; ++j) {
+                double* f = fb + (size_t)(hh * HALF + j) * 128 + L;
+                float2* gd = fd + (size_t)(hh * HALF + j) * 128 + L;
+                const float2 d2 = __ldcg(gd);
+                __stcg(f, __ldcg(f) + df_to_double(df{d2.x, d2.y}));
+                __stcg(gd, make_float2(0.0f, 0.0f));
+              }
+              nread = 0;
+            }
+            slicer_sync<TS>();  // every read of the blocks and of the old scales is done
+          }
+#pragma unroll
+          for (int h = 0; h < 2; ++h)
+            if (ey[h] > scale[c0 + h]) atomicMax(&scale[c0 + h], ey[h] + Sh::SLACK);
+          slicer_sync<TS>();
+          for (int cc = tid; cc < NC; cc += TS) {
+            const int sc = scale[cc];
+            pow2c[cc] = sc > 0 ? __int_as_float(max(1, min(254, sc - 895)) << 23) : 0.0f;  // 2^(s - 1022)
+          }
+        }
+        // eight digits of every Y element into buffer b (rows g, g + 8 of each 16-row block)
+#pragma unroll
+        for (int bi = 0; bi < 2; ++bi) {
+          const int rb = warp / NCB + bi * (16 / NCB);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int c = c0 + (e & 1), r = 16 * rb + g + 8 * (e >> 1);
+            const unsigned long long Nb = biased_fixed56<double>(yd[bi][e], scale[c]);
+            put_digits8_one<PLANE>(dig + (c >> 3) * SBO + (r >> 3) * LBO + (c & 7) * 16 + (r & 7) * 2, Nb);
+          }
+        }
+        if (tid == 0) ngrp[b] = grp == 0 ? 1 : 0;
+        fence_proxy_async_smem();  // the digit planes are read by the tensor core
+        tc_fence_before();         // the read-out's TMEM loads come before the next MMAs
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&dbar[b]);
+        cpar = (cpar & ~(1u << b)) | (bars.mpar & (1u << b));
+        bars.mpar ^= 1u << b;
+        last_b = b;
+        ++grp;
       }
-      if (tid == 0) ngrp[b] = grp == 0 ? 1 : 0;
-      fence_proxy_async_smem();  // the digit planes are read by the tensor core
-      tc_fence_before();         // the read-out's TMEM loads come before the next MMAs
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&dbar[b]);
-      cpar = (cpar & ~(1u << b)) | (bars.mpar & (1u << b));
-      bars.mpar ^= 1u << b;
-      last_b = b;
-      ++grp;
     }
     if (ok && grp > 0) {  // the last group
       if (!slicer_and<TS>(mbar_wait_bounded(&mbar[last_b], (cpar >> last_b) & 1u))) {
@@ -1989,24 +2239,25 @@ QL_DEV void gram_pipe_body(GramArgs<S> a, int bid, int k, uint32_t tbase, PipeBa
   gram_finish<NC, T, S, ArithDF>(a, smem, colmax, misc, k);
 }
 
-template <int NC, typename S>
+template <int NC, typename S, int XF = kXNone>
 __global__ void __launch_bounds__(PipeShape<NC>::T, 1)
     gram_pipe_kernel(const __grid_constant__ GramArgs<S> a, const __grid_constant__ CUtensorMap tmA,
                      const __grid_constant__ CUtensorMap tmB, int has_b) {
   extern __shared__ __align__(1024) unsigned char smem_umma[];
   const uint32_t tbase = pipe_cta_begin<NC, S>(smem_umma);
   PipeBars bars;
-  gram_pipe_body<NC, S>(a, blockIdx.x, gridDim.x, tbase, bars, &tmA, has_b ? &tmB : nullptr);
+  gram_pipe_body<NC, S, XF>(a, blockIdx.x, gridDim.x, tbase, bars, &tmA, has_b ? &tmB : nullptr);
   tc_fence_before();
   __syncthreads();
   if ((threadIdx.x >> 5) == 0) tmem_dealloc(tbase, PipeShape<NC>::TCOLS);
 }
 
-template <int NC, typename S>
-ql_status gram_pipe_launch_one(const GramCall& c, const GramWs& w) {
+// pass 1 (XF = kXNone) or a later pass (XF = kXUpper / kXFull, pass 2 or 3)
+template <int NC, typename S, int XF = kXNone>
+ql_status gram_pipe_launch_one(const GramCall& c, const GramWs& w, int pass = 1) {
   using Sh = PipeShape<NC>;
-  using Sm = PipeSmem<NC, S>;
-  auto kern = gram_pipe_kernel<NC, S>;
+  using Sm = PipeSmem<NC, S, XF>;
+  auto kern = gram_pipe_kernel<NC, S, XF>;
   static bool ready = false;
   static std::mutex mu;
   {
@@ -2030,7 +2281,7 @@ ql_status gram_pipe_launch_one(const GramCall& c, const GramWs& w) {
   a.m = c.m;
   a.n = c.n;
   a.tiles = tiles;
-  a.pass = 1;
+  a.pass = pass;
   a.method = c.method;
   a.gated = 0;
   a.epilogue = c.epilogue;
@@ -2127,10 +2378,13 @@ ql_status gram_dispatch(const GramCall& c, const GramWs& w, int gated) {
           ql_status st =
               pipe_gram_enabled() ? gram_pipe_launch_one<NC, S>(c, w) : gram_tc_launch_one<NC, S, kXNone>(c, w, 1);
           if (st) return st;
-          if (c.method == QL_SVQB2) return gram_tc_launch_one<NC, S, kXFull>(c, w, 2);
-          st = gram_tc_launch_one<NC, S, kXUpper>(c, w, 2);
+          // later passes: the pipelined kernel forms Y = X M' in its slicer warps
+          const bool pipe2 = pipe_gram_enabled() && pipe_gram2_enabled();
+          if (c.method == QL_SVQB2)
+            return pipe2 ? gram_pipe_launch_one<NC, S, kXFull>(c, w, 2) : gram_tc_launch_one<NC, S, kXFull>(c, w, 2);
+          st = pipe2 ? gram_pipe_launch_one<NC, S, kXUpper>(c, w, 2) : gram_tc_launch_one<NC, S, kXUpper>(c, w, 2);
           if (st || c.method != QL_SCHOLQR3) return st;
-          return gram_tc_launch_one<NC, S, kXUpper>(c, w, 3);
+          return pipe2 ? gram_pipe_launch_one<NC, S, kXUpper>(c, w, 3) : gram_tc_launch_one<NC, S, kXUpper>(c, w, 3);
         }
       }
     }

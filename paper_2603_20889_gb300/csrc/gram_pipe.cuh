@@ -36,6 +36,7 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include "gram.cuh"
 #include "gram_tc.cuh"
 #include "gram_umma.cuh"
 
@@ -64,7 +65,7 @@ struct PipeShape {
   static_assert((long long)G * KT * PAIRS_MAX * 4096 <= (1LL << 24), "exact FP32 digit sums");
 };
 
-template <int NC, typename S>
+template <int NC, typename S, int XF = kXNone>
 struct PipeSmem {
   using Sh = PipeShape<NC>;
   // a staged tile is KT / RPB boxes of RPB rows (128 bytes) x NC columns, written by the
@@ -87,7 +88,16 @@ struct PipeSmem {
   static constexpr size_t kMain = kOffSlot + 32;
   static constexpr size_t kRed = 8 * (size_t)128 * NC;       // end of chunk: per-lane sums (in the digits)
   static constexpr size_t kEpi = 8 * (4 * (size_t)NC * (NC + 1) + 8 * (NC + 1)) + 64 * 4 + 16;
-  static constexpr size_t kBytes = kMain;
+  // later passes (Y = X M'): the M' digits as mma.sync B fragments [8-column block][k-step]
+  // [digit][lane], the column exponents of X (whole matrix) and of M', and the CTA's entry
+  // decision
+  static constexpr int NCB = NC / 8, KSTEPS = NC / 16;
+  static constexpr size_t kOffBq = (kMain + 15) / 16 * 16;
+  static constexpr size_t kBq = XF == kXNone ? 0 : sizeof(uint2) * NCB * KSTEPS * 7 * 32;
+  static constexpr size_t kOffGexp = kOffBq + kBq;
+  static constexpr size_t kOffFexp = kOffGexp + 4 * NC;
+  static constexpr size_t kOffEntry = kOffFexp + 4 * NC;
+  static constexpr size_t kBytes = XF == kXNone ? kMain : kOffEntry + 16;
   static_assert(kEpi <= kOffPow, "the epilogue's shared memory stays below the scales and barriers");
   static_assert(kRed <= 2 * (size_t)Sh::DBUF, "per-lane sums fit in the digit buffers");
 };

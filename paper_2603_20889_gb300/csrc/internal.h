@@ -88,6 +88,9 @@ bool tc_gram_enabled();
 // First Gram pass of the 16-, 32- and 64-column classes on the pipelined tcgen05 kernel
 // (default; QL_GRAM_PIPE=0 selects the per-tile kernels, for comparison).
 bool pipe_gram_enabled();
+// QL_GRAM_PIPE2=0: the later Gram passes of n <= 32 run on the per-tile mma.sync kernel instead
+// of the pipelined one (A/B comparisons).
+bool pipe_gram2_enabled();
 // Tensor maps of the columns of [A b] for the pipelined Gram pass: A as a rank-2 tensor (rows
 // innermost, stride lda; boxes of 128 bytes of rows x all its columns, 128-byte swizzle) and
 // b as one unswizzled column; rows past m read as zeros.  tmB may be null (no b).  False, with the maps left
