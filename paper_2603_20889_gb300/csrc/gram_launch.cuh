@@ -2125,17 +2125,15 @@ QL_DEV void gram_pipe_body(GramArgs<S> a, int bid, int k, uint32_t tbase, PipeBa
           }
         }
         slicer_sync<TS>();  // every read of X's digits is done: buffer b takes Y's digits next
-        // Y against the running column scales (this lane holds columns c0 and c0 + 1)
+        // Y against the running column scales (this lane holds columns c0 and c0 + 1); the
+        // exponent of the high part bounds the double-float's (no FP64 instruction here: the
+        // FP64 pipe runs at 1/64 of the FP32 rate)
         const int c0 = cb * 8 + 2 * t4;
-        double yd[2][4];
         int ey[2] = {0, 0};
 #pragma unroll
         for (int bi = 0; bi < 2; ++bi)
 #pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            yd[bi][e] = df_to_double(y[bi][e]);
-            ey[e & 1] = max(ey[e & 1], elem_exponent(yd[bi][e]));
-          }
+          for (int e = 0; e < 4; ++e) ey[e & 1] = max(ey[e & 1], elem_exponent(y[bi][e].hi));
         const bool over = ey[0] > scale[c0] || ey[1] > scale[c0 + 1];
         const bool full = grp >= G;
         if (slicer_or<TS>(over) || full) {
@@ -2177,7 +2175,10 @@ QL_DEV void gram_pipe_body(GramArgs<S> a, int bid, int k, uint32_t tbase, PipeBa
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
             const int c = c0 + (e & 1), r = 16 * rb + g + 8 * (e >> 1);
-            const unsigned long long Nb = biased_fixed56<double>(yd[bi][e], scale[c]);
+            // fixed point of hi + lo: the two parts rounded separately (hi is exact unless the
+            // element lies 2^32 below its column's scale), one bias removed
+            const unsigned long long Nb = biased_fixed56<float>(y[bi][e].hi, scale[c]) +
+                                          biased_fixed56<float>(y[bi][e].lo, scale[c]) - kDigitBias8;
             put_digits8_one<PLANE>(dig + (c >> 3) * SBO + (r >> 3) * LBO + (c & 7) * 16 + (r & 7) * 2, Nb);
           }
         }
