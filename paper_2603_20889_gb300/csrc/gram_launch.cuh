@@ -1641,6 +1641,18 @@ ql_status gram_umma_launch_one(const GramCall& c, const GramWs& w, int pass) {
 // [tiles bid / k, tiles (bid + 1) / k) of one problem as partial `bid` of `k`, with the
 // tensor memory at tbase and the barriers that pipe_cta_begin set up; bars carries their
 // phase counts from one work item to the next.
+// The seven planes of the 48-bit convention (operands of Y = X M'), 8 rows per 16-byte store.
+template <int PLANE, int P = 0>
+QL_DEV void put_planes7(unsigned char* base, const unsigned long long (&Nb)[8]) {
+  uint4 w;
+  w.x = digit_word7<P>(Nb[0], Nb[1]);
+  w.y = digit_word7<P>(Nb[2], Nb[3]);
+  w.z = digit_word7<P>(Nb[4], Nb[5]);
+  w.w = digit_word7<P>(Nb[6], Nb[7]);
+  *reinterpret_cast<uint4*>(base + P * PLANE) = w;
+  if constexpr (P + 1 < 7) put_planes7<PLANE, P + 1>(base, Nb);
+}
+
 template <int NC, int PLANE, int P = 0>
 QL_DEV void put_planes8(unsigned char* base, const unsigned long long (&Nb)[8]) {
   uint4 w;
@@ -2052,25 +2064,18 @@ QL_DEV void gram_pipe_body(GramArgs<S> a, int bid, int k, uint32_t tbase, PipeBa
 #pragma unroll
             for (int j = 0; j < 8; ++j) xv[j] = S(0);
           }
-          long long Nb[8];
+          unsigned long long Nb[8];  // N + kDigitBias + kDigitTop7 >= 0 (see digit_word7)
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
+            long long N;
             if constexpr (sizeof(S) == 8) {
-              Nb[j] = (em > 0 ? fixed48_of_double((double)xv[j], em) : 0ll) + kDigitBias;
+              N = em > 0 ? fixed48_of_double((double)xv[j], em) : 0ll;
             } else {
-              Nb[j] = (em > 0 ? fixed48_of_float((float)xv[j], em - 896) : 0ll) + kDigitBias;
+              N = em > 0 ? fixed48_of_float((float)xv[j], em - 896) : 0ll;
             }
+            Nb[j] = (unsigned long long)(N + kDigitBias) + kDigitTop7;
           }
-          unsigned char* base = dig + (cu >> 3) * SBO + (r0_[uu] >> 3) * LBO + (cu & 7) * 16;
-#pragma unroll
-          for (int p = 0; p < 7; ++p) {
-            uint4 wv;
-            wv.x = bf16x2_of_ints(balanced_digit_rt(Nb[0], p), balanced_digit_rt(Nb[1], p));
-            wv.y = bf16x2_of_ints(balanced_digit_rt(Nb[2], p), balanced_digit_rt(Nb[3], p));
-            wv.z = bf16x2_of_ints(balanced_digit_rt(Nb[4], p), balanced_digit_rt(Nb[5], p));
-            wv.w = bf16x2_of_ints(balanced_digit_rt(Nb[6], p), balanced_digit_rt(Nb[7], p));
-            *reinterpret_cast<uint4*>(base + p * PLANE) = wv;
-          }
+          put_planes7<PLANE>(dig + (cu >> 3) * SBO + (r0_[uu] >> 3) * LBO + (cu & 7) * 16, Nb);
         }
         // stage b is read: the control warp may copy the tile two ahead into it
         fence_proxy_async_smem();

@@ -256,4 +256,19 @@ QL_DEV unsigned digit_word(unsigned long long A, unsigned long long B) {
   return *reinterpret_cast<const unsigned*>(&r);
 }
 
+// The same for the seven digits of the 48-bit convention (fixed48_of_double + kDigitBias,
+// see gram_tc.cuh) of two elements, given Nb7 = N + kDigitBias + kDigitTop7: the top digit's
+// field then reads (Nb7 >> 42) in [0, 128] and digit p's (Nb7 >> 7 (6 - p)) & 127.
+constexpr unsigned long long kDigitTop7 = 64ULL << 42;
+template <int P>
+QL_DEV unsigned digit_word7(unsigned long long A, unsigned long long B) {
+  constexpr int SH = 7 * (6 - P);
+  constexpr unsigned MASK = P == 0 ? 0x00ff00ffu : 0x007f007fu;
+  const unsigned fa = (unsigned)(A >> SH), fb = (unsigned)(B >> SH);
+  const unsigned w = (__byte_perm(fa, fb, 0x5410) & MASK) | 0x43004300u;
+  const __nv_bfloat162 r =
+      __hsub2(*reinterpret_cast<const __nv_bfloat162*>(&w), __floats2bfloat162_rn(192.0f, 192.0f));
+  return *reinterpret_cast<const unsigned*>(&r);
+}
+
 }  // namespace ql
